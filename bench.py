@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 tridiagonal partition solver.
+
+Default workload: one system of N = 2^26 unknowns, binary64 storage, the
+benchmark distribution (b ~ U[4,8], a, c ~ U[-1,1], x* ~ U[-1,1], d = A x*),
+sub-system size from the predictor.  A timed step is one binary64 solve
+(predictor lookup, Stage 1, the recursive interface solve, Stage 3) of that
+system with inputs resident in HBM; the inputs (2 GiB) exceed L2.  The same
+run also times the binary32 + binary64-refinement solve, binary32 storage,
+the plain one-thread-per-system GPU Thomas baseline, the 4096-system batched
+workload, the adjoint workload and the implicit heat step, and reports them
+under "variants".
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
+replica (independent problems, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_MAIN = 1 << 26
+METRIC = "unknowns solved/sec (FP64 partition solve, N=2^26)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# binary64 pipe: 2 FMA per clock per SM (the nominal 1.25 TFLOP/s over
+# 152 SMs at 2.07 GHz), 2 flops per FMA
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
+# algorithmic work per row of the binary64 Stage 1 (forward + backward sweep):
+# 8 FMA (pivot, 3 in the reciprocal, rhs, 3 backward) + 4 MUL -> 20 flops
+STAGE1_F64_FLOPS_PER_ROW = 20.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(value, world, device):
+    """Barrier, then the maximum of ``value`` over ranks."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    S = W.single(N_MAIN, seed=0)
+    # bounded sample: the whole system when the run stays within ~2 minutes
+    t0 = time.perf_counter()
+    oracle.thomas(S.a, S.b, S.c, S.d)
+    t_one = time.perf_counter() - t0
+    n_sample = N_MAIN if t_one * (args.steps + args.warmup) < 120 else max(1 << 20, int(N_MAIN * 120 / (
+        t_one * (args.steps + args.warmup))))
+    sl = slice(0, n_sample)
+    a, b, c, d = (np.ascontiguousarray(v[sl]) for v in (S.a, S.b, S.c, S.d))
+    for _ in range(args.warmup):
+        oracle.thomas(a, b, c, d)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.thomas(a, b, c, d)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_sample * args.steps / total
+    sample = f"oracle Thomas (binary64, one core) on the first {n_sample} rows of the N=2^26 system per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "single tridiagonal system N=2^26, binary64", "n": N_MAIN, "batch": 1},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def cuda_time(fn, steps, warmup, stream):
+    """Milliseconds per call over ``steps`` calls (CUDA events on ``stream``)."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def profile_kernels(tdp, fn, steps):
+    """{kernel: (launches, mean ms)} for ``steps`` calls (library event timing)."""
+    import torch
+
+    torch.cuda.synchronize()
+    tdp.tdp_profile_enable(True)
+    for _ in range(steps):
+        fn()
+    torch.cuda.synchronize()
+    prof = tdp.tdp_profile_summary()
+    tdp.tdp_profile_enable(False)
+    return {k: (v[0], v[1] / max(1, v[0])) for k, v in prof.items()}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2510_27351_gb300 as tdp
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    stream = torch.cuda.current_stream()
+    pk, pk_src = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+
+    # ---- inputs of the main workload (host, pinned copies for e2e) ----
+    t0 = time.time()
+    S = W.single(N_MAIN, seed=rank)
+    log(f"[bench] generated N=2^26 in {time.time() - t0:.1f}s")
+    host = {k: torch.from_numpy(getattr(S, k)).pin_memory() for k in ("a", "b", "c", "d")}
+    dev = {k: v.to(device, non_blocking=True) for k, v in host.items()}
+    x = torch.empty(N_MAIN, dtype=torch.float64, device=device)
+    torch.cuda.synchronize()
+    s_main = tdp.tdp_predict_s(N_MAIN, 1, tdp.F64)
+
+    def step_f64():
+        s = tdp.tdp_predict_s(N_MAIN, 1, tdp.F64)
+        tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, s, tdp.F64, 0, stream)
+
+    # correctness guard on the timed configuration (vs x*)
+    step_f64()
+    torch.cuda.synchronize()
+    err_xstar = float((x.cpu().numpy() - S.xstar).__abs__().max() / np.abs(S.xstar).max())
+
+    launches0 = tdp.tdp_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step_f64()
+        torch.cuda.synchronize()
+        barrier_max(0.0, world, device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches_a = tdp.tdp_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_f64()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches_b = tdp.tdp_launch_count()
+        ms = e0.elapsed_time(e1) / args.steps
+    ms = barrier_max(ms, world, device)
+    clocks = clk.summary()
+    value = world * N_MAIN / (ms * 1e-3)
+    gpu_launches = launches_b - launches_a
+
+    # ---- roofline of the dominant kernel (library event timing of the same step) ----
+    prof = profile_kernels(tdp, step_f64, max(3, min(args.steps, 10)))
+    dom = max(prof.items(), key=lambda kv: kv[1][0] * kv[1][1])
+    st1 = prof.get("stage1_keep_f64")
+    roof = None
+    if st1:
+        flops = STAGE1_F64_FLOPS_PER_ROW * N_MAIN
+        ach = flops / (st1[1] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA/clk x 2 flop",
+                "algorithmic_bytes_per_row": 56 + 64 / s_main,
+                "hbm_frac_of_kernel": (56 + 64 / s_main) * N_MAIN / (st1[1] * 1e-3) / 1e9 / hbm_peak}
+    solve_hbm_frac = value / world * 40 / 1e9 / hbm_peak
+
+    # ---- end to end through the public API with host buffers ----
+    host_x = torch.empty(N_MAIN, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        for k in ("a", "b", "c", "d"):
+            dev[k].copy_(host[k], non_blocking=True)
+        step_f64()
+        host_x.copy_(x, non_blocking=True)
+
+    e2e_ms = cuda_time(step_e2e, max(3, args.steps // 2), 2, stream)
+    e2e_ms = barrier_max(e2e_ms, world, device)
+    e2e = {"value": world * N_MAIN / (e2e_ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": 4 * 8 * N_MAIN,
+           "d2h_bytes_per_step": 8 * N_MAIN, "ms_per_step": e2e_ms}
+
+    variants = {}
+    if not args.main_only:
+        variants = run_variants(args, tdp, S, dev, x, stream, hbm_peak, device)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(S)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single tridiagonal system N=2^26, binary64, b~U[4,8], a,c~U[-1,1], d=A x*",
+                       "n": N_MAIN, "batch": 1, "s": s_main, "parallelism": f"replicas{world}",
+                       "l2": "inputs (2 GiB) larger than L2; no flush"},
+            "roofline": roof, "hbm_frac_of_whole_solve": solve_hbm_frac, "peaks_source": pk_src,
+            "hbm_peak_gbs": hbm_peak, "kernels_ms": {k: v[1] for k, v in prof.items()},
+            "dominant_kernel": dom[0], "rel_err_vs_xstar": err_xstar, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks, "cpu_baseline": cpu, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline(S):
+    import oracle
+
+    t_end = time.perf_counter() + 10.0
+    reps, t = 0, 0.0
+    while time.perf_counter() < t_end or reps == 0:
+        t0 = time.perf_counter()
+        oracle.thomas(S.a, S.b, S.c, S.d)
+        t += time.perf_counter() - t0
+        reps += 1
+    return {"value": reps * N_MAIN / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle Thomas (binary64) on the full N=2^26 system, {reps} repetitions (~10 s)"}
+
+
+def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
+    import torch
+
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    import oracle
+
+    def hbm(ms, bytes_):
+        return bytes_ / (ms * 1e-3) / 1e9 / hbm_peak
+
+    # binary32 + binary64 refinement on the same system (binary64 storage)
+    s_r = tdp.tdp_predict_s(N_MAIN, 1, tdp.F32_REFINE)
+    fn = lambda: tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, s_r, tdp.F32_REFINE, 1, stream)
+    ms = cuda_time(fn, steps, 2, stream)
+    fn()
+    torch.cuda.synchronize()
+    err = float(np.abs(x.cpu().numpy() - S.xstar).max() / np.abs(S.xstar).max())
+    prof = profile_kernels(tdp, fn, 3)
+    out["fp32_refine1"] = {"ms": ms, "unknowns_per_s": N_MAIN / (ms * 1e-3), "hbm_frac_40B": hbm(ms, 40 * N_MAIN),
+                           "s": s_r, "rel_err_vs_xstar": err, "kernels_ms": {k: v[1] for k, v in prof.items()}}
+    # binary32 storage
+    s_f = tdp.tdp_predict_s(N_MAIN, 1, tdp.F32)
+    d32 = {k: v.float() for k, v in dev.items()}
+    x32 = torch.empty(N_MAIN, dtype=torch.float32, device=device)
+    fn = lambda: tdp.tdp_solve(d32["a"], d32["b"], d32["c"], d32["d"], x32, N_MAIN, s_f, tdp.F32, 0, stream)
+    ms = cuda_time(fn, steps, 2, stream)
+    err = float(np.abs(x32.double().cpu().numpy() - S.xstar).max() / np.abs(S.xstar).max())
+    prof = profile_kernels(tdp, fn, 3)
+    out["fp32"] = {"ms": ms, "unknowns_per_s": N_MAIN / (ms * 1e-3), "hbm_frac_20B": hbm(ms, 20 * N_MAIN), "s": s_f,
+                   "rel_err_vs_xstar": err, "kernels_ms": {k: v[1] for k, v in prof.items()}}
+    del d32, x32
+    # plain GPU Thomas, one thread per system: rate measured on the first 2^16 rows
+    nt = 1 << 16
+    off = torch.tensor([0, nt], dtype=torch.int64, device=device)
+    sl = {k: v[:nt].contiguous() for k, v in dev.items()}
+    xt = torch.empty(nt, dtype=torch.float64, device=device)
+    fn = lambda: tdp.tdp_thomas_batched(off, 1, nt, sl["a"], sl["b"], sl["c"], sl["d"], xt, tdp.F64, stream)
+    ms = cuda_time(fn, 2, 1, stream)
+    out["thomas_gpu_single"] = {"ms_for_2^16_rows": ms, "unknowns_per_s": nt / (ms * 1e-3),
+                                "note": "one GPU thread runs sequential Thomas; rate independent of N"}
+    del sl, xt
+    # batched: 4096 systems, N log-uniform in [64, 65536]
+    Sb = W.batched(4096, 64, 65536, seed=0)
+    bdev = {k: torch.from_numpy(getattr(Sb, k)).to(device) for k in ("a", "b", "c", "d")}
+    boff = torch.from_numpy(Sb.offsets).to(device)
+    bx = torch.empty(Sb.n, dtype=torch.float64, device=device)
+    res = {"total_n": Sb.n}
+    for name, code, it in (("fp64", tdp.F64, 0), ("fp32_refine1", tdp.F32_REFINE, 1)):
+        fn = lambda: tdp.tdp_solve_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx, 0,
+                                           code, it, stream)
+        ms = cuda_time(fn, steps, 2, stream)
+        res[name] = {"ms": ms, "unknowns_per_s": Sb.n / (ms * 1e-3), "hbm_frac_40B": hbm(ms, 40 * Sb.n),
+                     "s": tdp.tdp_predict_s(Sb.n // Sb.batch, Sb.batch, code)}
+    fn = lambda: tdp.tdp_thomas_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx,
+                                        tdp.F64, stream)
+    ms = cuda_time(fn, 2, 1, stream)
+    res["thomas_gpu"] = {"ms": ms, "unknowns_per_s": Sb.n / (ms * 1e-3)}
+    out["batched_4096"] = res
+    del bdev, bx
+    # adjoint: 1024 systems of 8192, loss weights w ~ N(0,1)
+    Sa = W.uniform_batch(1024, 8192, seed=0)
+    adev = {k: torch.from_numpy(getattr(Sa, k)).to(device) for k in ("a", "b", "c", "d")}
+    aoff = torch.from_numpy(Sa.offsets).to(device)
+    ax = torch.empty(Sa.n, dtype=torch.float64, device=device)
+    tdp.tdp_solve_batched(aoff, Sa.batch, Sa.n, adev["a"], adev["b"], adev["c"], adev["d"], ax, 0, tdp.F64, 0,
+                          stream)
+    g = torch.from_numpy(W.loss_weights(Sa.n, seed=0)).to(device)
+    grads = [torch.empty_like(ax) for _ in range(4)]
+    fn = lambda: tdp.tdp_solve_backward(aoff, Sa.batch, Sa.n, adev["a"], adev["b"], adev["c"], ax, g, *grads, 0,
+                                        tdp.F64, stream)
+    ms = cuda_time(fn, steps, 2, stream)
+    out["adjoint_1024x8192"] = {"ms": ms, "unknowns_per_s": Sa.n / (ms * 1e-3),
+                                "hbm_frac_72B": hbm(ms, 72 * Sa.n)}
+    del adev, ax, grads
+    # implicit heat step on 2048^2: row sweep then column sweep
+    H = W.heat(2048, 0.5, seed=0)
+    hd = {k: torch.from_numpy(np.ascontiguousarray(getattr(H, k)).reshape(-1)).to(device) for k in ("a", "b", "c", "u")}
+    r1 = torch.empty_like(hd["u"])
+    r2 = torch.empty_like(hd["u"])
+
+    def heat():
+        tdp.tdp_solve_strided(2048, 2048, 2048, 1, hd["a"], hd["b"], hd["c"], hd["u"], r1, 0, tdp.F32_REFINE, 1,
+                              stream)
+        tdp.tdp_solve_strided(2048, 2048, 1, 2048, hd["a"], hd["b"], hd["c"], r1, r2, 0, tdp.F32_REFINE, 1, stream)
+
+    ms = cuda_time(heat, steps, 2, stream)
+    out["heat_2048"] = {"ms": ms, "unknowns_per_s": 2 * 2048 * 2048 / (ms * 1e-3), "dtype": "fp32_refine1"}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--main-only", action="store_true", help="skip the variant workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3")
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

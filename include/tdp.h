@@ -1,0 +1,170 @@
+/*
+ * tdp.h -- C ABI of the GB300 tridiagonal partition solver.
+ *
+ * Method: the parallel partition method for tridiagonal systems (Veneva,
+ * "ML-Based Optimum Sub-system Size for the GPU Implementation of the
+ * Tridiagonal Partition Method", arXiv 2510.27351, Sec. I): the N unknowns
+ * are split into sub-systems of s rows; Stage 1 reduces every sub-system to
+ * two interface equations, Stage 2 solves the tridiagonal interface system,
+ * Stage 3 substitutes the interface values and solves the interiors.  The
+ * sub-system size s is chosen by a 1-nearest-neighbour model over measured
+ * timings (Sec. II-E) when the caller passes s = 0.
+ *
+ * Matrix convention: row i reads  a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i];
+ * a[0] and c[n-1] of every system are ignored (need not be zero).
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller and
+ * aligned to 16 bytes; the library never frees or retains it.  Inputs are
+ * read-only; x must not alias an input.  Scratch memory (the interface
+ * system and the per-row coefficients kept between stages) comes from a
+ * library-owned workspace per CUDA stream, grown on demand; it cannot grow
+ * while the stream is being captured into a CUDA graph, so call tdp_reserve
+ * (or run the call once) before capturing.
+ *
+ * Streams: every call is asynchronous on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream) and makes no host synchronisation unless checked
+ * mode is on (tdp_set_checked) or the workspace has to grow.
+ *
+ * Errors: every int-returning call returns one of the TDP_* codes below and
+ * records a message retrievable with tdp_last_error() (per host thread).
+ * Pivot failures found on the device (a zero or non-finite pivot) are
+ * recorded in a per-stream device status word; they are returned as
+ * TDP_ESINGULAR by the call itself in checked mode, else by tdp_status().
+ */
+#ifndef TDP_H
+#define TDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Precision of a solve.
+ *  TDP_F64        binary64 storage, binary64 arithmetic.
+ *  TDP_F32        binary32 storage, binary32 arithmetic for the sub-system
+ *                 eliminations and substitutions, binary64 interface solve.
+ *  TDP_F32_REFINE binary64 storage; binary32 eliminations/substitutions with a
+ *                 binary64 residual r = d - A x and correction x += delta
+ *                 (iterative refinement), binary64 interface solve. */
+typedef enum { TDP_F64 = 0, TDP_F32 = 1, TDP_F32_REFINE = 2 } tdp_dtype;
+
+#define TDP_OK 0
+#define TDP_EINVAL 1     /* bad argument: size, s, null or misaligned pointer, offsets */
+#define TDP_ECUDA 2      /* a CUDA runtime call or kernel launch failed */
+#define TDP_ESINGULAR 3  /* a zero or non-finite pivot was met on the device */
+#define TDP_ETIMEOUT 4   /* a bounded device wait ran out */
+#define TDP_ENOMEM 5     /* workspace too small and cannot grow (e.g. during capture) */
+
+/* Solve one system of n unknowns (Sec. I, three stages).
+ *  a, b, c, d : device arrays of n elements (binary64 for TDP_F64 and
+ *               TDP_F32_REFINE, binary32 for TDP_F32).
+ *  x          : device array of n elements, same type; receives the solution.
+ *  n          : number of unknowns, n >= 1.
+ *  s          : sub-system size, 2 <= s <= 1024, or 0 to let tdp_predict_s
+ *               choose (Sec. II-E).  s >= n solves the system as one block.
+ *  refine_iters: for TDP_F32_REFINE, number of binary64-residual corrections
+ *               (0..8); ignored otherwise.
+ * Returns TDP_OK or an error code. */
+int tdp_solve(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
+              tdp_dtype dtype, int32_t refine_iters, void* stream);
+
+/* Solve `batch` independent systems stored back to back.
+ *  offsets    : DEVICE array of batch+1 int64, offsets[0] = 0, non-decreasing;
+ *               system j occupies rows offsets[j] .. offsets[j+1]-1.
+ *  total_n    : offsets[batch] (passed by value so that no copy to the host is
+ *               needed; the device checks it and reports TDP_EINVAL through
+ *               the status word when it disagrees).
+ *  s          : sub-system size for every system (2..1024), or 0 to use the
+ *               tuned per-size table (tdp_predict_s per system).
+ * Empty systems are allowed.  Other arguments as tdp_solve. */
+int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                      const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
+                      void* stream);
+
+/* Solve `batch` systems of n unknowns each with arbitrary element strides:
+ * element i of system j lives at index  j*sys_stride + i*elem_stride  of each
+ * array (in elements).  sys_stride = n, elem_stride = 1 is a contiguous batch;
+ * sys_stride = 1, elem_stride = batch is the interleaved layout of the column
+ * sweep of an alternating-direction implicit step.  The index ranges of
+ * different systems must not overlap. */
+int tdp_solve_strided(int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
+                      const void* b, const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype,
+                      int32_t refine_iters, void* stream);
+
+/* Adjoint of the solve (not in the paper).  Given the forward solution x of
+ * A x = d and g = dL/dx, computes lambda = A^{-T} g with the same partition
+ * kernels and the gradients of L:
+ *   grad_d = lambda,  grad_a[i] = -lambda[i] x[i-1] (0 at a system's first row),
+ *   grad_b[i] = -lambda[i] x[i],  grad_c[i] = -lambda[i] x[i+1] (0 at its last row).
+ *  offsets    : DEVICE array of batch+1 int64 (batch = 1, offsets = {0, n} for
+ *               a single system); total_n = offsets[batch].
+ *  grad_*     : device arrays of total_n elements; any may be NULL to skip it
+ *               (grad_d is lambda and is computed even when NULL is passed
+ *               for it, into workspace).
+ * dtype TDP_F64 or TDP_F32. */
+int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                       const void* c, const void* x, const void* g, void* grad_a, void* grad_b, void* grad_c,
+                       void* grad_d, int32_t s, tdp_dtype dtype, void* stream);
+
+/* Sub-system size for a solve of `batch` systems of about n unknowns each
+ * (Sec. II-E: 1-nearest-neighbour over (log2 n, log2 batch) in the table of
+ * the given precision, ties to the larger s).  Uses the table loaded by
+ * tdp_load_table, else the built-in table measured on GB300, else the
+ * paper's interval rule (Sec. II-D).  Never fails: returns a valid s >= 2. */
+int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype);
+
+/* Replace the predictor's table (text: lines "dtype n batch s", '#' comments;
+ * dtype 0/1/2 as tdp_dtype); an empty path "" restores the built-in table.
+ * Returns TDP_OK or TDP_EINVAL (unreadable file or bad row; the table is
+ * then unchanged). */
+int tdp_load_table(const char* path);
+
+/* Grow the workspace of `stream` to what a solve of `total_n` unknowns in
+ * `batch` systems with sub-system size s (0 = smallest supported) needs, so
+ * that later calls of that size make no allocation (required before CUDA
+ * graph capture).  May synchronise the stream. */
+int tdp_reserve(int64_t total_n, int32_t batch, int32_t s, tdp_dtype dtype, void* stream);
+
+/* Read and clear the device status word of `stream` (synchronises it).
+ * Returns TDP_OK, TDP_ESINGULAR, TDP_ETIMEOUT or TDP_EINVAL. */
+int tdp_status(void* stream);
+
+/* Checked mode: when on, every solve synchronises its stream and returns the
+ * device status.  Default off. */
+void tdp_set_checked(int on);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* tdp_last_error(void);
+
+/* Number of kernels this library has launched in this process (all
+ * streams); lets callers count launches inside a timed region. */
+int64_t tdp_launch_count(void);
+
+/* Per-kernel timing (a tracing aid): when enabled, every kernel the library
+ * launches outside stream capture is bracketed by two CUDA events recorded
+ * on its launch stream.  Enabling (or disabling) clears earlier records. */
+void tdp_profile_enable(int on);
+
+/* Waits for the recorded events and writes one line per kernel name,
+ * "name launches total_ms", in first-launch order, into buf (NUL-terminated,
+ * truncated to len-1 bytes).  Returns the full text length. */
+int64_t tdp_profile_summary(char* buf, int64_t len);
+
+/* Plain GPU Thomas baseline: one thread per system, sequential Thomas.
+ * Same arguments as tdp_solve_batched (TDP_F64 or TDP_F32). */
+int tdp_thomas_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                       const void* c, const void* d, void* x, tdp_dtype dtype, void* stream);
+
+/* Diagnostics: run Stage 1 only on one system and write its interface
+ * system (2*ceil(n/s) rows, binary64, row 2k for x[k*s], row 2k+1 for the
+ * last row of block k; a one-row last block gets an identity row 2k+1).
+ * ra..rd are device arrays of at least 2*ceil(n/s) doubles. */
+int tdp_stage1(const void* a, const void* b, const void* c, const void* d, int64_t n, int32_t s, tdp_dtype dtype,
+               double* ra, double* rb, double* rc, double* rd, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDP_H */

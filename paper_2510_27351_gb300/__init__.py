@@ -1,0 +1,250 @@
+"""GB300 tridiagonal partition solver: Python binding of the C ABI (include/tdp.h).
+
+Every numerical step runs in the CUDA kernels of ``libtdp.so``; this module
+only marshals arguments (torch tensors -> device pointers, the current torch
+stream) and raises on error codes.  There is no CPU fallback: importing the
+package fails when the library cannot be loaded, and every call needs CUDA
+tensors.
+
+Names follow the C ABI (``tdp_solve``, ``tdp_solve_batched``, ...); the
+lower-case helpers ``solve``, ``solve_batched``, ... allocate the output and
+pick defaults.  ``TridiagonalSolve`` is the autograd Function (forward: the
+partition solve; backward: the transposed solve of ``tdp_solve_backward``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+F64, F32, F32_REFINE = 0, 1, 2
+_ERRORS = {1: "EINVAL", 2: "ECUDA", 3: "ESINGULAR", 4: "ETIMEOUT", 5: "ENOMEM"}
+
+
+class TdpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"TDP_{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path) or os.environ.get("TDP_REBUILD") == "1":
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.tdp_solve.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
+    lib.tdp_solve_batched.argtypes = [P, I32, I64, P, P, P, P, P, I32, I32, I32, P]
+    lib.tdp_solve_strided.argtypes = [I32, I64, I64, I64, P, P, P, P, P, I32, I32, I32, P]
+    lib.tdp_solve_backward.argtypes = [P, I32, I64, P, P, P, P, P, P, P, P, P, I32, I32, P]
+    lib.tdp_predict_s.argtypes = [I64, I32, I32]
+    lib.tdp_predict_s.restype = I32
+    lib.tdp_load_table.argtypes = [ctypes.c_char_p]
+    lib.tdp_reserve.argtypes = [I64, I32, I32, I32, P]
+    lib.tdp_status.argtypes = [P]
+    lib.tdp_set_checked.argtypes = [ctypes.c_int]
+    lib.tdp_set_checked.restype = None
+    lib.tdp_last_error.restype = ctypes.c_char_p
+    lib.tdp_launch_count.restype = I64
+    lib.tdp_thomas_batched.argtypes = [P, I32, I64, P, P, P, P, P, I32, P]
+    lib.tdp_stage1.argtypes = [P, P, P, P, I64, I32, I32, P, P, P, P, P]
+    lib.tdp_profile_enable.argtypes = [ctypes.c_int]
+    lib.tdp_profile_enable.restype = None
+    lib.tdp_profile_summary.argtypes = [ctypes.c_char_p, I64]
+    lib.tdp_profile_summary.restype = I64
+    return lib
+
+
+LIB = _load()
+
+# Every symbol the header declares (checked by the tests).
+SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_backward", "tdp_predict_s",
+           "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
+           "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary")
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise TdpError(rc, LIB.tdp_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("tdp: tensors must live on a CUDA device (no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("tdp: tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _dtype_code(t: torch.Tensor, refine: bool) -> int:
+    if t.dtype == torch.float64:
+        return F32_REFINE if refine else F64
+    if t.dtype == torch.float32:
+        if refine:
+            raise ValueError("tdp: refinement needs float64 storage")
+        return F32
+    raise TypeError(f"tdp: unsupported dtype {t.dtype}")
+
+
+# ----------------------------------------------------------------------------
+# C ABI, one to one (tensors or raw device pointers)
+# ----------------------------------------------------------------------------
+def tdp_solve(a, b, c, d, x, n, s, dtype, refine_iters=0, stream=None):
+    _check(LIB.tdp_solve(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), int(n), int(s), int(dtype),
+                         int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_batched(offsets, batch, total_n, a, b, c, d, x, s, dtype, refine_iters=0, stream=None):
+    _check(LIB.tdp_solve_batched(_ptr(offsets), int(batch), int(total_n), _ptr(a), _ptr(b), _ptr(c), _ptr(d),
+                                 _ptr(x), int(s), int(dtype), int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_strided(batch, n, sys_stride, elem_stride, a, b, c, d, x, s, dtype, refine_iters=0, stream=None):
+    _check(LIB.tdp_solve_strided(int(batch), int(n), int(sys_stride), int(elem_stride), _ptr(a), _ptr(b), _ptr(c),
+                                 _ptr(d), _ptr(x), int(s), int(dtype), int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_backward(offsets, batch, total_n, a, b, c, x, g, grad_a, grad_b, grad_c, grad_d, s, dtype,
+                       stream=None):
+    _check(LIB.tdp_solve_backward(_ptr(offsets), int(batch), int(total_n), _ptr(a), _ptr(b), _ptr(c), _ptr(x),
+                                  _ptr(g), _ptr(grad_a), _ptr(grad_b), _ptr(grad_c), _ptr(grad_d), int(s),
+                                  int(dtype), _stream(stream)))
+
+
+def tdp_thomas_batched(offsets, batch, total_n, a, b, c, d, x, dtype, stream=None):
+    _check(LIB.tdp_thomas_batched(_ptr(offsets), int(batch), int(total_n), _ptr(a), _ptr(b), _ptr(c), _ptr(d),
+                                  _ptr(x), int(dtype), _stream(stream)))
+
+
+def tdp_stage1(a, b, c, d, n, s, dtype, ra, rb, rc, rd, stream=None):
+    _check(LIB.tdp_stage1(_ptr(a), _ptr(b), _ptr(c), _ptr(d), int(n), int(s), int(dtype), _ptr(ra), _ptr(rb),
+                          _ptr(rc), _ptr(rd), _stream(stream)))
+
+
+def tdp_predict_s(n: int, batch: int = 1, dtype: int = F64) -> int:
+    return int(LIB.tdp_predict_s(int(n), int(batch), int(dtype)))
+
+
+def tdp_load_table(path: str):
+    _check(LIB.tdp_load_table(path.encode()))
+
+
+def tdp_reserve(total_n, batch, s, dtype, stream=None):
+    _check(LIB.tdp_reserve(int(total_n), int(batch), int(s), int(dtype), _stream(stream)))
+
+
+def tdp_status(stream=None):
+    _check(LIB.tdp_status(_stream(stream)))
+
+
+def tdp_set_checked(on: bool):
+    LIB.tdp_set_checked(1 if on else 0)
+
+
+def tdp_last_error() -> str:
+    return LIB.tdp_last_error().decode()
+
+
+def tdp_launch_count() -> int:
+    return int(LIB.tdp_launch_count())
+
+
+def tdp_profile_enable(on: bool):
+    LIB.tdp_profile_enable(1 if on else 0)
+
+
+def tdp_profile_summary() -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded since
+    profiling was enabled (waits for their events)."""
+    n = int(LIB.tdp_profile_summary(None, 0))
+    buf = ctypes.create_string_buffer(n + 1)
+    LIB.tdp_profile_summary(buf, n + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Convenience wrappers
+# ----------------------------------------------------------------------------
+def solve(a, b, c, d, s: int = 0, refine: bool = False, refine_iters: int = 1, out=None, stream=None):
+    """x with A x = d for one system (CUDA tensors of equal length and dtype)."""
+    x = torch.empty_like(d) if out is None else out
+    tdp_solve(a, b, c, d, x, d.numel(), s, _dtype_code(d, refine), refine_iters if refine else 0, stream)
+    return x
+
+
+def solve_batched(offsets, a, b, c, d, s: int = 0, refine: bool = False, refine_iters: int = 1, out=None,
+                  stream=None):
+    """Systems stored back to back; ``offsets`` is an int64 CUDA tensor of B+1 entries."""
+    x = torch.empty_like(d) if out is None else out
+    tdp_solve_batched(offsets, offsets.numel() - 1, d.numel(), a, b, c, d, x, s, _dtype_code(d, refine),
+                      refine_iters if refine else 0, stream)
+    return x
+
+
+def solve_strided(batch, n, sys_stride, elem_stride, a, b, c, d, s: int = 0, refine: bool = False,
+                  refine_iters: int = 1, out=None, stream=None):
+    x = torch.empty_like(d) if out is None else out
+    tdp_solve_strided(batch, n, sys_stride, elem_stride, a, b, c, d, x, s, _dtype_code(d, refine),
+                      refine_iters if refine else 0, stream)
+    return x
+
+
+def thomas_batched(offsets, a, b, c, d, out=None, stream=None):
+    x = torch.empty_like(d) if out is None else out
+    tdp_thomas_batched(offsets, offsets.numel() - 1, d.numel(), a, b, c, d, x, _dtype_code(d, False), stream)
+    return x
+
+
+def solve_backward(offsets, a, b, c, x, g, s: int = 0, stream=None):
+    """(grad_a, grad_b, grad_c, grad_d) of L given x = A^{-1} d and g = dL/dx."""
+    ga, gb, gc, gd = (torch.empty_like(x) for _ in range(4))
+    tdp_solve_backward(offsets, offsets.numel() - 1, x.numel(), a, b, c, x, g, ga, gb, gc, gd, s,
+                       _dtype_code(x, False), stream)
+    return ga, gb, gc, gd
+
+
+class TridiagonalSolve(torch.autograd.Function):
+    """x = A^{-1} d for back-to-back systems; differentiable in a, b, c, d.
+
+    The forward pass keeps x; the backward pass solves A^T lambda = g with the
+    same partition kernels and forms the diagonal gradients on the device.
+    """
+
+    @staticmethod
+    def forward(ctx, offsets, a, b, c, d, s=0):
+        x = solve_batched(offsets, a, b, c, d, s=s)
+        ctx.save_for_backward(offsets, a, b, c, x)
+        ctx.s = s
+        return x
+
+    @staticmethod
+    def backward(ctx, g):
+        offsets, a, b, c, x = ctx.saved_tensors
+        ga, gb, gc, gd = solve_backward(offsets, a, b, c, x, g.contiguous(), s=ctx.s)
+        return None, ga, gb, gc, gd, None
+
+
+def tridiagonal_solve(a, b, c, d, offsets=None, s: int = 0):
+    """Differentiable solve; ``offsets`` defaults to one system."""
+    if offsets is None:
+        offsets = torch.tensor([0, d.numel()], dtype=torch.int64, device=d.device)
+    return TridiagonalSolve.apply(offsets, a, b, c, d, s)

@@ -1,0 +1,449 @@
+// C ABI of the solver: argument checks, per-stream workspace, error
+// reporting, the sub-system-size predictor (Sec. II-E) and its table.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "tdp_internal.h"
+
+namespace tdp {
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_checked{0};
+
+struct Workspace {
+  char* buf = nullptr;
+  size_t cap = 0;
+  unsigned* status = nullptr;
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_ptrs(std::initializer_list<const void*> ptrs, const char* fn) {
+  for (const void* p : ptrs) {
+    if (!p) return set_error(TDP_EINVAL, std::string(fn) + ": null pointer");
+    if (!aligned16(p)) return set_error(TDP_EINVAL, std::string(fn) + ": pointer not 16-byte aligned");
+  }
+  return TDP_OK;
+}
+
+int check_common(int64_t n, int32_t s, tdp_dtype dt, int32_t iters, const char* fn, bool allow_refine = true) {
+  if (n < 1) return set_error(TDP_EINVAL, std::string(fn) + ": n must be >= 1");
+  if (s != 0 && (s < 2 || s > 1024)) return set_error(TDP_EINVAL, std::string(fn) + ": s must be 0 or in [2, 1024]");
+  if (dt != TDP_F64 && dt != TDP_F32 && !(allow_refine && dt == TDP_F32_REFINE))
+    return set_error(TDP_EINVAL, std::string(fn) + ": unsupported dtype");
+  if (iters < 0 || iters > 8) return set_error(TDP_EINVAL, std::string(fn) + ": refine_iters must be in [0, 8]");
+  return TDP_OK;
+}
+
+Workspace* workspace_for(cudaStream_t st, int* dev_out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  *dev_out = dev;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  return &g_ws[{dev, st}];
+}
+
+// Run a driver twice: a dry run that sizes the workspace, then the real one.
+template <typename F>
+int run(void* stream, const char* fn, F&& driver) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  Workspace* ws = workspace_for(st, &dev);
+  Arena sizing;
+  Ctx dry;
+  dry.stream = st;
+  dry.ar = &sizing;
+  dry.dry = true;
+  driver(dry);
+  const size_t need = sizing.off + 256;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": bad stream");
+  if (!ws->status || need > ws->cap) {
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_error(TDP_ENOMEM, std::string(fn) + ": workspace must be reserved before stream capture (need " +
+                                       std::to_string(need) + " bytes)");
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));
+    if (!ws->status) {
+      e = cudaMalloc(&ws->status, 256);
+      if (e == cudaSuccess) e = cudaMemset(ws->status, 0, 256);
+      if (e != cudaSuccess) return set_error(TDP_ENOMEM, std::string(fn) + ": status word: " + cudaGetErrorString(e));
+    }
+    if (need > ws->cap) {
+      if (ws->buf) cudaFree(ws->buf);
+      ws->buf = nullptr;
+      ws->cap = 0;
+      const size_t grow = need + need / 8;
+      e = cudaMalloc(&ws->buf, grow);
+      if (e != cudaSuccess) {
+        ws->buf = nullptr;
+        cudaGetLastError();
+        return set_error(TDP_ENOMEM, std::string(fn) + ": workspace of " + std::to_string(grow) +
+                                         " bytes: " + cudaGetErrorString(e));
+      }
+      ws->cap = grow;
+    }
+  }
+  Arena arena;
+  arena.base = ws->buf;
+  arena.cap = ws->cap;
+  Ctx ctx;
+  ctx.stream = st;
+  ctx.status = ws->status;
+  ctx.ar = &arena;
+  driver(ctx);
+  if (ctx.err != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + ctx.msg);
+  if (g_checked.load()) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));
+    unsigned h = 0;
+    e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));
+    if (h & ST_BADARG) return set_error(TDP_EINVAL, std::string(fn) + ": offsets rejected on the device");
+    if (h & ST_TIMEOUT) return set_error(TDP_ETIMEOUT, std::string(fn) + ": device wait timed out");
+    if (h & ST_SINGULAR) return set_error(TDP_ESINGULAR, std::string(fn) + ": zero or non-finite pivot");
+  }
+  g_last_error.clear();
+  return TDP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Predictor table: rows (dtype, n, batch, s).  The built-in rows are the
+// labels measured on GB300 by the sweep shipped with the Python package; when
+// a dtype has no rows the paper's interval rule (Sec. II-D) is used.
+// ---------------------------------------------------------------------------
+struct Row {
+  int dt;
+  double n, batch;
+  int s;
+};
+
+#include "tdp_table.inc"
+
+std::mutex g_tab_mu;
+std::vector<Row> g_table;
+bool g_table_init = false;
+std::vector<float> g_feat[3];
+std::vector<int32_t> g_lab[3];
+
+void ensure_table() {
+  if (g_table_init) return;
+  for (const Row& r : kBuiltinTable) g_table.push_back(r);
+  g_table_init = true;
+}
+
+int interval_rule(double n) {
+  // Sec. II-D, FP64 on RTX 2080 Ti
+  if (n <= 4.5e3) return 4;
+  if (n <= 2.5e4) return 8;
+  if (n <= 5e4) return 16;
+  if (n <= 7.5e4) return 20;
+  if (n <= 1e7) return 32;
+  return 64;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launch counting and event-based per-kernel timing.
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+std::atomic<int> g_prof_on{0};
+std::vector<ProfRec> g_prof;
+thread_local cudaEvent_t t_open = nullptr;
+thread_local const char* t_open_name = nullptr;
+}  // namespace
+
+void launch_begin(cudaStream_t st, const char* name) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  t_open = nullptr;
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  cudaEvent_t e0;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  cudaEventRecord(e0, st);
+  t_open = e0;
+  t_open_name = name;
+}
+
+void launch_end(cudaStream_t st) {
+  if (!t_open) return;
+  cudaEvent_t e1;
+  if (cudaEventCreate(&e1) != cudaSuccess) return;
+  cudaEventRecord(e1, st);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(ProfRec{t_open_name, t_open, e1});
+  t_open = nullptr;
+}
+
+void profile_clear() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_prof) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  g_prof.clear();
+}
+
+std::string profile_text() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  std::vector<std::string> order;
+  for (auto& r : g_prof) {
+    cudaEventSynchronize(r.e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    auto it = agg.find(r.name);
+    if (it == agg.end()) {
+      order.push_back(r.name);
+      agg[r.name] = {1, double(ms)};
+    } else {
+      it->second.first += 1;
+      it->second.second += ms;
+    }
+  }
+  std::ostringstream os;
+  for (auto& k : order) os << k << ' ' << agg[k].first << ' ' << agg[k].second << '\n';
+  return os.str();
+}
+
+int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  ensure_table();
+  const double ln = std::log2(double(n < 1 ? 1 : n));
+  const double lb = std::log2(double(batch < 1 ? 1 : batch));
+  double best = 1e300;
+  int s = 0;
+  for (const Row& r : g_table) {
+    if (r.dt != int(dt)) continue;
+    const double dn = std::log2(r.n) - ln, db = std::log2(r.batch) - lb;
+    const double dist = dn * dn + db * db;
+    if (dist < best || (dist == best && r.s > s)) {
+      best = dist;
+      s = r.s;
+    }
+  }
+  if (s < 2) s = interval_rule(double(n));
+  return s;
+}
+
+int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  ensure_table();
+  auto& f = g_feat[int(dt)];
+  auto& l = g_lab[int(dt)];
+  f.clear();
+  l.clear();
+  for (const Row& r : g_table) {
+    if (r.dt != int(dt)) continue;
+    f.push_back(float(std::log2(r.n)));
+    f.push_back(float(std::log2(r.batch)));
+    l.push_back(r.s);
+  }
+  *feat = f.data();
+  *labels = l.data();
+  return int(l.size());
+}
+
+int load_table_file(const char* path) {
+  if (path[0] == '\0') {  // restore the built-in table
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    g_table.clear();
+    g_table_init = false;
+    ensure_table();
+    return TDP_OK;
+  }
+  std::ifstream in(path);
+  if (!in) return set_error(TDP_EINVAL, std::string("tdp_load_table: cannot open ") + path);
+  std::vector<Row> rows;
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t h = line.find('#');
+    if (h != std::string::npos) line.resize(h);
+    std::istringstream ss(line);
+    Row r;
+    if (!(ss >> r.dt >> r.n >> r.batch >> r.s)) continue;
+    if (r.dt < 0 || r.dt > 2 || r.n < 1 || r.batch < 1 || r.s < 2 || r.s > 1024)
+      return set_error(TDP_EINVAL, "tdp_load_table: bad row: " + line);
+    rows.push_back(r);
+  }
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  g_table = rows;
+  g_table_init = true;
+  return TDP_OK;
+}
+
+}  // namespace tdp
+
+using namespace tdp;
+
+extern "C" {
+
+int tdp_solve(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
+              tdp_dtype dtype, int32_t refine_iters, void* stream) {
+  int rc = check_common(n, s, dtype, refine_iters, "tdp_solve");
+  if (rc) return rc;
+  if ((rc = check_ptrs({a, b, c, d, x}, "tdp_solve"))) return rc;
+  const int ss = s ? s : predict_s(n, 1, dtype);
+  return run(stream, "tdp_solve", [&](Ctx& ctx) { solve_single(ctx, a, b, c, d, x, n, ss, dtype, refine_iters); });
+}
+
+int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                      const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
+                      void* stream) {
+  if (batch < 1) return set_error(TDP_EINVAL, "tdp_solve_batched: batch must be >= 1");
+  if (total_n < 0) return set_error(TDP_EINVAL, "tdp_solve_batched: total_n must be >= 0");
+  int rc = check_common(total_n < 1 ? 1 : total_n, s, dtype, refine_iters, "tdp_solve_batched");
+  if (rc) return rc;
+  if (!offsets) return set_error(TDP_EINVAL, "tdp_solve_batched: null offsets");
+  if (total_n == 0) return TDP_OK;
+  if ((rc = check_ptrs({a, b, c, d, x}, "tdp_solve_batched"))) return rc;
+  const int ss = s ? s : predict_s((total_n + batch - 1) / batch, batch, dtype);
+  return run(stream, "tdp_solve_batched", [&](Ctx& ctx) {
+    solve_batched(ctx, offsets, batch, total_n, a, b, c, d, x, ss, dtype, refine_iters);
+  });
+}
+
+int tdp_solve_strided(int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
+                      const void* b, const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype,
+                      int32_t refine_iters, void* stream) {
+  if (batch < 1) return set_error(TDP_EINVAL, "tdp_solve_strided: batch must be >= 1");
+  int rc = check_common(n, s, dtype, refine_iters, "tdp_solve_strided");
+  if (rc) return rc;
+  if (sys_stride < 0 || elem_stride < 1) return set_error(TDP_EINVAL, "tdp_solve_strided: bad strides");
+  if ((rc = check_ptrs({a, b, c, d, x}, "tdp_solve_strided"))) return rc;
+  const int ss = s ? s : predict_s(n, batch, dtype);
+  return run(stream, "tdp_solve_strided", [&](Ctx& ctx) {
+    solve_strided(ctx, batch, n, sys_stride, elem_stride, a, b, c, d, x, ss, dtype, refine_iters);
+  });
+}
+
+int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                       const void* c, const void* x, const void* g, void* grad_a, void* grad_b, void* grad_c,
+                       void* grad_d, int32_t s, tdp_dtype dtype, void* stream) {
+  if (batch < 1) return set_error(TDP_EINVAL, "tdp_solve_backward: batch must be >= 1");
+  int rc = check_common(total_n < 1 ? 1 : total_n, s, dtype, 0, "tdp_solve_backward", false);
+  if (rc) return rc;
+  if (!offsets) return set_error(TDP_EINVAL, "tdp_solve_backward: null offsets");
+  if (total_n == 0) return TDP_OK;
+  if ((rc = check_ptrs({a, b, c, x, g}, "tdp_solve_backward"))) return rc;
+  for (const void* p : {(const void*)grad_a, (const void*)grad_b, (const void*)grad_c, (const void*)grad_d})
+    if (p && !aligned16(p)) return set_error(TDP_EINVAL, "tdp_solve_backward: gradient not 16-byte aligned");
+  const int ss = s ? s : predict_s((total_n + batch - 1) / batch, batch, dtype);
+  return run(stream, "tdp_solve_backward", [&](Ctx& ctx) {
+    solve_backward(ctx, offsets, batch, total_n, a, b, c, x, g, grad_a, grad_b, grad_c, grad_d, ss, dtype);
+  });
+}
+
+int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype) {
+  if (dtype != TDP_F64 && dtype != TDP_F32 && dtype != TDP_F32_REFINE) dtype = TDP_F64;
+  return predict_s(n, batch, dtype);
+}
+
+int tdp_load_table(const char* path) {
+  if (!path) return set_error(TDP_EINVAL, "tdp_load_table: null path");
+  return load_table_file(path);
+}
+
+int tdp_reserve(int64_t total_n, int32_t batch, int32_t s, tdp_dtype dtype, void* stream) {
+  if (total_n < 1 || batch < 1) return set_error(TDP_EINVAL, "tdp_reserve: sizes must be >= 1");
+  if (s == 0) s = 2;
+  int rc = check_common(total_n, s, dtype, 0, "tdp_reserve");
+  if (rc) return rc;
+  // size for the largest consumer: a batched refined solve with 8 corrections
+  return run(stream, "tdp_reserve", [&](Ctx& ctx) {
+    if (!ctx.dry) return;
+    solve_batched(ctx, nullptr, batch, total_n, nullptr, nullptr, nullptr, nullptr, nullptr, s, dtype,
+                  dtype == TDP_F32_REFINE ? 8 : 0);
+    solve_backward(ctx, nullptr, batch, total_n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                   nullptr, nullptr, s, dtype == TDP_F32_REFINE ? TDP_F64 : dtype);
+  });
+}
+
+int tdp_status(void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  Workspace* ws = workspace_for(st, &dev);
+  if (!ws->status) return TDP_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string("tdp_status: ") + cudaGetErrorString(e));
+  unsigned h = 0;
+  e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string("tdp_status: ") + cudaGetErrorString(e));
+  if (h & ST_BADARG) return set_error(TDP_EINVAL, "tdp_status: offsets rejected on the device");
+  if (h & ST_TIMEOUT) return set_error(TDP_ETIMEOUT, "tdp_status: device wait timed out");
+  if (h & ST_SINGULAR) return set_error(TDP_ESINGULAR, "tdp_status: zero or non-finite pivot");
+  return TDP_OK;
+}
+
+void tdp_set_checked(int on) { g_checked.store(on ? 1 : 0); }
+
+const char* tdp_last_error(void) { return g_last_error.c_str(); }
+
+int64_t tdp_launch_count(void) { return g_launches.load(); }
+
+void tdp_profile_enable(int on) {
+  profile_clear();
+  g_prof_on.store(on ? 1 : 0);
+}
+
+int64_t tdp_profile_summary(char* buf, int64_t len) {
+  const std::string txt = profile_text();
+  if (buf && len > 0) {
+    const size_t k = std::min<size_t>(txt.size(), size_t(len - 1));
+    std::memcpy(buf, txt.data(), k);
+    buf[k] = '\0';
+  }
+  return int64_t(txt.size());
+}
+
+int tdp_thomas_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                       const void* c, const void* d, void* x, tdp_dtype dtype, void* stream) {
+  if (batch < 1) return set_error(TDP_EINVAL, "tdp_thomas_batched: batch must be >= 1");
+  int rc = check_common(total_n < 1 ? 1 : total_n, 2, dtype, 0, "tdp_thomas_batched", false);
+  if (rc) return rc;
+  if (!offsets) return set_error(TDP_EINVAL, "tdp_thomas_batched: null offsets");
+  if (total_n == 0) return TDP_OK;
+  if ((rc = check_ptrs({a, b, c, d, x}, "tdp_thomas_batched"))) return rc;
+  return run(stream, "tdp_thomas_batched",
+             [&](Ctx& ctx) { thomas_batched(ctx, offsets, batch, total_n, a, b, c, d, x, dtype); });
+}
+
+int tdp_stage1(const void* a, const void* b, const void* c, const void* d, int64_t n, int32_t s, tdp_dtype dtype,
+               double* ra, double* rb, double* rc, double* rd, void* stream) {
+  int r = check_common(n, s == 0 ? 2 : s, dtype, 0, "tdp_stage1");
+  if (r) return r;
+  if ((r = check_ptrs({a, b, c, d, ra, rb, rc, rd}, "tdp_stage1"))) return r;
+  const int ss = s ? s : predict_s(n, 1, dtype);
+  return run(stream, "tdp_stage1", [&](Ctx& ctx) { stage1_only(ctx, a, b, c, d, n, ss, dtype, ra, rb, rc, rd); });
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Host-side interfaces between the C ABI (tdp_api.cu) and the solver
+// drivers (tdp_solver.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/tdp.h"
+#include "tdp_status.h"
+
+namespace tdp {
+
+// Bump allocator over a workspace buffer.  With base == nullptr it only
+// measures (dry run used to size the workspace before any launch).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T) + 16;
+    return p;
+  }
+};
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  unsigned* status = nullptr;  // device status word
+  Arena* ar = nullptr;
+  bool dry = false;            // size the workspace only, launch nothing
+  cudaError_t err = cudaSuccess;
+  int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
+  int s_rec = 32;              // sub-system size inside the interface-system recursion
+  std::string msg;
+  void fail(cudaError_t e, const char* where) {
+    if (err == cudaSuccess && e != cudaSuccess) {
+      err = e;
+      msg = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+  }
+};
+
+// Launch bookkeeping: counts every kernel launch and, when profiling is on,
+// brackets it with CUDA events on the launch stream (tdp_profile_*).
+void launch_begin(cudaStream_t st, const char* name);
+void launch_end(cudaStream_t st);
+
+// Drivers.  Every pointer is a device pointer; all work is queued on ctx.stream.
+void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                  int s, tdp_dtype dt, int refine_iters);
+void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
+                   const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
+void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
+                   const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
+void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
+                    const void* b, const void* c, const void* x, const void* g, void* ga, void* gb, void* gc,
+                    void* gd, int s, tdp_dtype dt);
+void thomas_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
+                    const void* b, const void* c, const void* d, void* x, tdp_dtype dt);
+void stage1_only(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, int64_t n, int s,
+                 tdp_dtype dt, double* ra, double* rb, double* rc, double* rd);
+
+// Predictor (host 1-NN over the loaded table; tdp_api.cu).
+int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);
+// Flattened table for the device-side predictor: rows of (log2 n, log2 batch, s) per dtype.
+int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels);
+
+}  // namespace tdp

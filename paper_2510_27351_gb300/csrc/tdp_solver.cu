@@ -1,0 +1,532 @@
+// Solver drivers: launch geometry, workspace layout and the order of the
+// stages of the partition method (Sec. I), for single, batched, strided and
+// transposed (adjoint) solves.
+#include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "tdp_internal.h"
+#include "tdp_kernels.cuh"
+
+namespace tdp {
+
+namespace {
+
+constexpr int kMaxSmem = 227 * 1024;
+constexpr int64_t kBaseRows = 64;  // interface systems this small go to one thread
+
+unsigned magic_for(int s) { return unsigned((uint64_t(1) << 32) / uint64_t(s) + 1); }
+
+// Opt every tile kernel in to the full shared memory once (per kernel and device).
+template <typename K>
+void allow_smem(K kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<int, const void*> key{dev, reinterpret_cast<const void*>(kernel)};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(key)) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  done.insert(key);
+}
+
+// Threads (= blocks) per CTA for a tile kernel holding `arrays` tiles of
+// `elem` bytes per row, plus 4 bytes per row of owner table when mapped.
+int pick_threads(const Ctx& ctx, int s, int arrays, int elem, bool mapped, size_t* smem_out) {
+  auto bytes = [&](int T) {
+    return size_t(arrays) * elem * size_t(s) * (T + 1) + (mapped ? size_t(4) * T * s : 0);
+  };
+  int T = 256;
+  while (T > 32 && bytes(T) > size_t(ctx.smem_budget)) T /= 2;
+  while (T > 1 && bytes(T) > size_t(kMaxSmem)) --T;
+  *smem_out = bytes(T);
+  return T;
+}
+
+void pre_launch(Ctx& ctx, const char* what) { launch_begin(ctx.stream, what); }
+
+void post_launch(Ctx& ctx, const char* what) {
+  launch_end(ctx.stream);
+  ctx.fail(cudaGetLastError(), what);
+}
+
+template <typename C>
+const char* tname(const char* f64, const char* f32) {
+  return sizeof(C) == 8 ? f64 : f32;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename S, typename C, bool MAPPED, bool KEEP>
+void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
+            const int64_t* blk, double* ra, double* rb, double* rc, double* rd, C* ka, C* kg, C* kd) {
+  if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  size_t smem;
+  const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
+  auto kern = k_stage1<S, C, MAPPED, KEEP>;
+  allow_smem(kern);
+  const int64_t grid = (m + T - 1) / T;
+  pre_launch(ctx, KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32"));
+  kern<<<unsigned(grid), T, smem, ctx.stream>>>(a, b, c, d, n, s, magic_for(s), m, blk, ra, rb, rc, rd, ka, kg,
+                                                kd, ctx.status);
+  post_launch(ctx, "stage 1");
+}
+
+template <typename C, typename S, bool MAPPED>
+void stage3_kept(Ctx& ctx, const C* ka, const C* kg, const C* kd, int64_t n, int s, int64_t m, const int64_t* blk,
+                 const double* y, S* x) {
+  if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  size_t smem;
+  const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);  // same tiling as Stage 1
+  const size_t need = size_t(2) * T * sizeof(C) + (MAPPED ? size_t(4) * T * s : 0);
+  auto kern = k_stage3_kept<C, S, MAPPED>;
+  allow_smem(kern);
+  const int64_t grid = (m + T - 1) / T;
+  pre_launch(ctx, "stage3_kept_f64");
+  kern<<<unsigned(grid), T, need, ctx.stream>>>(ka, kg, kd, n, s, magic_for(s), m, blk, y, x);
+  post_launch(ctx, "stage 3");
+}
+
+template <typename S, typename C, bool MAPPED>
+void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
+                    const int64_t* blk, const double* y, S* x) {
+  if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  size_t smem;
+  const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
+  auto kern = k_stage3_resolve<S, C, MAPPED>;
+  allow_smem(kern);
+  const int64_t grid = (m + T - 1) / T;
+  pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
+  kern<<<unsigned(grid), T, smem, ctx.stream>>>(a, b, c, d, n, s, magic_for(s), m, blk, y, x, ctx.status);
+  post_launch(ctx, "stage 3");
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: the interface system (M rows, binary64) is solved by applying the
+// partition method to it again (the recursive variant, Sec. III) until it is
+// small enough for one thread.
+// ---------------------------------------------------------------------------
+void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
+                     int64_t M) {
+  if (M <= 0) return;
+  if (M <= kBaseRows) {
+    double* scratch = ctx.ar->take<double>(M);
+    if (ctx.dry || ctx.err != cudaSuccess) return;
+    pre_launch(ctx, "interface_base");
+    k_thomas<double, double><<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, nullptr, 1, M, 0, 1, M, scratch,
+                                                        ctx.status);
+    post_launch(ctx, "interface base solve");
+    return;
+  }
+  const int s2 = ctx.s_rec;
+  const int64_t m2 = (M + s2 - 1) / s2;
+  double* ka = ctx.ar->take<double>(M);
+  double* kg = ctx.ar->take<double>(M);
+  double* kd = ctx.ar->take<double>(M);
+  double* ra2 = ctx.ar->take<double>(2 * m2);
+  double* rb2 = ctx.ar->take<double>(2 * m2);
+  double* rc2 = ctx.ar->take<double>(2 * m2);
+  double* rd2 = ctx.ar->take<double>(2 * m2);
+  double* y2 = ctx.ar->take<double>(2 * m2);
+  stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd);
+  solve_interface(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
+  stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y);
+}
+
+// ---------------------------------------------------------------------------
+// Helper kernels: block map, residual, update, transposition, gradients.
+// ---------------------------------------------------------------------------
+
+// bbase[j] = number of blocks before system j (exclusive scan of
+// ceil(N_j / s)); bbase[batch] = total.  Invalid offsets (offsets[0] != 0,
+// decreasing, or offsets[batch] != total_n) make every count zero and raise
+// ST_BADARG, so that no later kernel touches a row.
+__global__ void __launch_bounds__(1024) k_block_scan(const int64_t* __restrict__ off, int32_t batch, int s,
+                                                     int64_t total_n, int64_t* __restrict__ bbase,
+                                                     unsigned* __restrict__ status) {
+  __shared__ int64_t warp_sums[32];
+  __shared__ int bad;
+  __shared__ int64_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    bad = (off[0] != 0 || off[batch] != total_n) ? 1 : 0;
+    carry = 0;
+  }
+  __syncthreads();
+  for (int64_t j = tid; j < batch; j += blockDim.x)
+    if (off[j + 1] < off[j]) bad = 1;
+  __syncthreads();
+  if (bad) {
+    for (int64_t j = tid; j <= batch; j += blockDim.x) bbase[j] = 0;
+    if (tid == 0) flag(status, ST_BADARG);
+    return;
+  }
+  for (int64_t j0 = 0; j0 < batch; j0 += blockDim.x) {
+    const int64_t j = j0 + tid;
+    const int64_t len = (j < batch) ? off[j + 1] - off[j] : 0;
+    int64_t v = (len + s - 1) / s;
+    // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t w = (lane < int(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const int64_t incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+    const int64_t excl = incl - ((j < batch) ? (off[j + 1] - off[j] + s - 1) / s : 0);
+    if (j < batch) bbase[j] = excl;
+    __syncthreads();
+    if (tid == int(blockDim.x) - 1) carry = incl;
+    __syncthreads();
+  }
+  if (tid == 0) bbase[batch] = carry;
+}
+
+// blk[k] for k < m_max: start row of block k with flags; dummy blocks (after
+// the last real one) start at total_n and are empty.  blk[m_max] = total_n.
+__global__ void k_block_fill(const int64_t* __restrict__ off, int32_t batch, int s, int64_t total_n,
+                             const int64_t* __restrict__ bbase, int64_t m_max, int64_t* __restrict__ blk) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k > m_max) return;
+  if (k == m_max || k >= bbase[batch]) {
+    blk[k] = total_n;
+    return;
+  }
+  // system j with bbase[j] <= k < bbase[j+1]
+  int32_t lo = 0, hi = batch - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (bbase[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  const int64_t i = k - bbase[lo];
+  const int64_t cnt = bbase[lo + 1] - bbase[lo];
+  int64_t e = off[lo] + i * s;
+  if (i == 0) e |= BLK_FIRST;
+  if (i == cnt - 1) e |= BLK_LAST;
+  blk[k] = e;
+}
+
+// r = d - A x in binary64 for a batch described by blk (system ends from the
+// block flags); x of a neighbouring system is never read.
+template <bool MAPPED>
+__global__ void k_residual(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                           const double* __restrict__ d, const double* __restrict__ x, double* __restrict__ r,
+                           int64_t n, const uint8_t* __restrict__ edge) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint8_t e = MAPPED ? edge[i] : uint8_t((i == 0 ? 1 : 0) | (i == n - 1 ? 2 : 0));
+    double acc = fma(-b[i], x[i], d[i]);
+    if (!(e & 1) && i > 0) acc = fma(-a[i], x[i - 1], acc);
+    if (!(e & 2) && i < n - 1) acc = fma(-c[i], x[i + 1], acc);
+    r[i] = acc;
+  }
+}
+
+__global__ void k_add(double* __restrict__ x, const double* __restrict__ dx, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += dx[i];
+}
+
+// edge[i]: bit 0 = first row of its system, bit 1 = last row.
+__global__ void k_edges(const int64_t* __restrict__ off, int32_t batch, uint8_t* __restrict__ edge,
+                        int64_t total_n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  const int64_t s0 = off[j], s1 = off[j + 1];
+  if (s1 <= s0 || s0 < 0 || s1 > total_n) return;
+  edge[s0] |= 1;
+  edge[s1 - 1] |= 2;
+}
+
+// Transposed diagonals: aT[i] = c[i-1], cT[i] = a[i+1] within each system.
+template <typename S>
+__global__ void k_transpose(const S* __restrict__ a, const S* __restrict__ c, S* __restrict__ aT,
+                            S* __restrict__ cT, int64_t n, const uint8_t* __restrict__ edge) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint8_t e = edge[i];
+    aT[i] = ((e & 1) || i == 0) ? S(0) : c[i - 1];
+    cT[i] = ((e & 2) || i == n - 1) ? S(0) : a[i + 1];
+  }
+}
+
+// grad_a = -lam x[i-1], grad_b = -lam x, grad_c = -lam x[i+1] (zero at system ends).
+template <typename S>
+__global__ void k_grads(const S* __restrict__ lam, const S* __restrict__ x, S* __restrict__ ga, S* __restrict__ gb,
+                        S* __restrict__ gc, int64_t n, const uint8_t* __restrict__ edge) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint8_t e = edge[i];
+    const S l = lam[i];
+    if (ga) ga[i] = ((e & 1) || i == 0) ? S(0) : -l * x[i - 1];
+    if (gb) gb[i] = -l * x[i];
+    if (gc) gc[i] = ((e & 2) || i == n - 1) ? S(0) : -l * x[i + 1];
+  }
+}
+
+// Uniform offsets j * n for strided batches copied to contiguous storage.
+__global__ void k_iota_offsets(int64_t* __restrict__ off, int32_t batch, int64_t n) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j <= batch) off[j] = j * n;
+}
+
+template <typename S>
+__global__ void k_gather(const S* __restrict__ src, S* __restrict__ dst, int32_t batch, int64_t n, int64_t ss,
+                         int64_t es) {
+  const int64_t total = int64_t(batch) * n;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = q / n, i = q - j * n;
+    dst[q] = src[j * ss + i * es];
+  }
+}
+
+template <typename S>
+__global__ void k_scatter(const S* __restrict__ src, S* __restrict__ dst, int32_t batch, int64_t n, int64_t ss,
+                          int64_t es) {
+  const int64_t total = int64_t(batch) * n;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = q / n, i = q - j * n;
+    dst[j * ss + i * es] = src[q];
+  }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
+}
+
+// ---------------------------------------------------------------------------
+// One solve over blocks given either arithmetically (one system) or by blk.
+// ---------------------------------------------------------------------------
+template <bool MAPPED>
+void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
+                  int64_t m, const int64_t* blk, const uint8_t* edge, tdp_dtype dt, int refine_iters) {
+  double* ra = ctx.ar->take<double>(2 * m);
+  double* rb = ctx.ar->take<double>(2 * m);
+  double* rc = ctx.ar->take<double>(2 * m);
+  double* rd = ctx.ar->take<double>(2 * m);
+  double* y = ctx.ar->take<double>(2 * m);
+  if (dt == TDP_F64) {
+    using T = double;
+    const T *A = (const T*)a, *B = (const T*)b, *Cc = (const T*)c, *D = (const T*)d;
+    double* ka = ctx.ar->take<double>(n);
+    double* kg = ctx.ar->take<double>(n);
+    double* kd = ctx.ar->take<double>(n);
+    stage1<T, T, MAPPED, true>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, ka, kg, kd);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    stage3_kept<T, T, MAPPED>(ctx, ka, kg, kd, n, s, m, blk, y, (T*)x);
+  } else if (dt == TDP_F32) {
+    using T = float;
+    const T *A = (const T*)a, *B = (const T*)b, *Cc = (const T*)c, *D = (const T*)d;
+    stage1<T, T, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (T*)nullptr, (T*)nullptr,
+                                (T*)nullptr);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    stage3_resolve<T, T, MAPPED>(ctx, A, B, Cc, D, n, s, m, blk, y, (T*)x);
+  } else {
+    // binary32 eliminations, binary64 residual and correction
+    const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
+    double* X = (double*)x;
+    double* r = ctx.ar->take<double>(refine_iters > 0 ? n : 1);
+    double* dx = ctx.ar->take<double>(refine_iters > 0 ? n : 1);
+    stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                         (float*)nullptr, (float*)nullptr);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    stage3_resolve<double, float, MAPPED>(ctx, A, B, Cc, D, n, s, m, blk, y, X);
+    for (int it = 0; it < refine_iters; ++it) {
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "residual_f64");
+        k_residual<MAPPED><<<grid_for(n, 256), 256, 0, ctx.stream>>>(A, B, Cc, D, X, r, n, edge);
+        post_launch(ctx, "residual");
+      }
+      stage1<double, float, MAPPED, false>(ctx, A, B, Cc, r, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                           (float*)nullptr, (float*)nullptr);
+      solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+      stage3_resolve<double, float, MAPPED>(ctx, A, B, Cc, r, n, s, m, blk, y, dx);
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "update_f64");
+        k_add<<<grid_for(n, 256), 256, 0, ctx.stream>>>(X, dx, n);
+        post_launch(ctx, "update");
+      }
+    }
+  }
+}
+
+struct BatchMap {
+  const int64_t* blk = nullptr;
+  const uint8_t* edge = nullptr;
+  int64_t m = 0;
+};
+
+BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, int s, bool need_edges) {
+  BatchMap bm;
+  bm.m = (total_n + int64_t(batch) * (s - 1)) / s;
+  int64_t* bbase = ctx.ar->take<int64_t>(batch + 1);
+  int64_t* blk = ctx.ar->take<int64_t>(bm.m + 1);
+  uint8_t* edge = need_edges ? ctx.ar->take<uint8_t>(total_n) : nullptr;
+  bm.blk = blk;
+  bm.edge = edge;
+  if (ctx.dry || ctx.err != cudaSuccess) return bm;
+  pre_launch(ctx, "block_scan");
+  k_block_scan<<<1, 1024, 0, ctx.stream>>>(offsets, batch, s, total_n, bbase, ctx.status);
+  post_launch(ctx, "block scan");
+  pre_launch(ctx, "block_fill");
+  k_block_fill<<<unsigned((bm.m + 1 + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, s, total_n, bbase, bm.m,
+                                                                         blk);
+  post_launch(ctx, "block fill");
+  if (need_edges && total_n > 0) {
+    ctx.fail(cudaMemsetAsync(edge, 0, size_t(total_n), ctx.stream), "edge clear");
+    pre_launch(ctx, "edges");
+    k_edges<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, edge, total_n);
+    post_launch(ctx, "edges");
+  }
+  return bm;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Public drivers
+// ---------------------------------------------------------------------------
+void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
+                  tdp_dtype dt, int refine_iters) {
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  const int64_t m = (n + s - 1) / s;
+  solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
+}
+
+void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                   const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
+  if (batch <= 0 || total_n <= 0) return;
+  BatchMap bm = build_map(ctx, offsets, batch, total_n, s, dt == TDP_F32_REFINE && refine_iters > 0);
+  solve_blocks<true>(ctx, a, b, c, d, x, total_n, s, bm.m, bm.blk, bm.edge, dt, refine_iters);
+}
+
+void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, const void* a, const void* b,
+                   const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
+  if (batch <= 0 || n <= 0) return;
+  const int64_t total = int64_t(batch) * n;
+  int64_t* off = ctx.ar->take<int64_t>(batch + 1);
+  const bool contiguous = (es == 1 && ss == n);
+  const size_t el = (dt == TDP_F32) ? 4 : 8;
+  void* g[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (!contiguous)
+    for (int i = 0; i < 5; ++i) g[i] = ctx.ar->take<char>(total * el);  // each 256-byte aligned
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    pre_launch(ctx, "offsets");
+    k_iota_offsets<<<unsigned((batch + 256) / 256), 256, 0, ctx.stream>>>(off, batch, n);
+    post_launch(ctx, "offsets");
+  }
+  if (contiguous) {
+    solve_batched(ctx, off, batch, total, a, b, c, d, x, s, dt, refine_iters);
+    return;
+  }
+  const void* src[4] = {a, b, c, d};
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    for (int i = 0; i < 4; ++i) {
+      pre_launch(ctx, "gather");
+      if (el == 8)
+        k_gather<double><<<grid_for(total, 256), 256, 0, ctx.stream>>>((const double*)src[i], (double*)g[i], batch,
+                                                                       n, ss, es);
+      else
+        k_gather<float><<<grid_for(total, 256), 256, 0, ctx.stream>>>((const float*)src[i], (float*)g[i], batch, n,
+                                                                      ss, es);
+      post_launch(ctx, "gather");
+    }
+  }
+  solve_batched(ctx, off, batch, total, g[0], g[1], g[2], g[3], g[4], s, dt, refine_iters);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    pre_launch(ctx, "scatter");
+    if (el == 8)
+      k_scatter<double><<<grid_for(total, 256), 256, 0, ctx.stream>>>((const double*)g[4], (double*)x, batch, n, ss,
+                                                                      es);
+    else
+      k_scatter<float><<<grid_for(total, 256), 256, 0, ctx.stream>>>((const float*)g[4], (float*)x, batch, n, ss,
+                                                                     es);
+    post_launch(ctx, "scatter");
+  }
+}
+
+void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                    const void* c, const void* x, const void* g, void* ga, void* gb, void* gc, void* gd, int s,
+                    tdp_dtype dt) {
+  if (batch <= 0 || total_n <= 0) return;
+  const size_t el = (dt == TDP_F32) ? 4 : 8;
+  uint8_t* edge = ctx.ar->take<uint8_t>(total_n);
+  char* aT = ctx.ar->take<char>(total_n * el);
+  char* cT = ctx.ar->take<char>(total_n * el);
+  char* lam = gd ? (char*)gd : ctx.ar->take<char>(total_n * el);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    ctx.fail(cudaMemsetAsync(edge, 0, size_t(total_n), ctx.stream), "edge clear");
+    pre_launch(ctx, "edges");
+    k_edges<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, edge, total_n);
+    post_launch(ctx, "edges");
+    pre_launch(ctx, "transpose");
+    if (el == 8)
+      k_transpose<double><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const double*)a, (const double*)c,
+                                                                          (double*)aT, (double*)cT, total_n, edge);
+    else
+      k_transpose<float><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const float*)a, (const float*)c,
+                                                                         (float*)aT, (float*)cT, total_n, edge);
+    post_launch(ctx, "transpose");
+  }
+  solve_batched(ctx, offsets, batch, total_n, aT, b, cT, g, lam, s, dt, 0);
+  if (!ctx.dry && ctx.err == cudaSuccess && (ga || gb || gc)) {
+    pre_launch(ctx, "gradients");
+    if (el == 8)
+      k_grads<double><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const double*)lam, (const double*)x,
+                                                                      (double*)ga, (double*)gb, (double*)gc, total_n,
+                                                                      edge);
+    else
+      k_grads<float><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const float*)lam, (const float*)x, (float*)ga,
+                                                                     (float*)gb, (float*)gc, total_n, edge);
+    post_launch(ctx, "gradients");
+  }
+}
+
+void thomas_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                    const void* c, const void* d, void* x, tdp_dtype dt) {
+  if (batch <= 0 || total_n <= 0) return;
+  const size_t el = (dt == TDP_F32) ? 4 : 8;
+  char* scratch = ctx.ar->take<char>(total_n * el);
+  if (ctx.dry || ctx.err != cudaSuccess) return;
+  const unsigned grid = unsigned((batch + 127) / 128);
+  pre_launch(ctx, dt == TDP_F32 ? "thomas_f32" : "thomas_f64");
+  if (dt == TDP_F32)
+    k_thomas<float, float><<<grid, 128, 0, ctx.stream>>>((const float*)a, (const float*)b, (const float*)c,
+                                                         (const float*)d, (float*)x, offsets, batch, 0, 0, 1,
+                                                         total_n, (float*)scratch, ctx.status);
+  else
+    k_thomas<double, double><<<grid, 128, 0, ctx.stream>>>((const double*)a, (const double*)b, (const double*)c,
+                                                           (const double*)d, (double*)x, offsets, batch, 0, 0, 1,
+                                                           total_n, (double*)scratch, ctx.status);
+  post_launch(ctx, "thomas");
+}
+
+void stage1_only(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, int64_t n, int s,
+                 tdp_dtype dt, double* ra, double* rb, double* rc, double* rd) {
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  const int64_t m = (n + s - 1) / s;
+  if (dt == TDP_F64)
+    stage1<double, double, false, false>(ctx, (const double*)a, (const double*)b, (const double*)c,
+                                         (const double*)d, n, s, m, nullptr, ra, rb, rc, rd, (double*)nullptr,
+                                         (double*)nullptr, (double*)nullptr);
+  else if (dt == TDP_F32)
+    stage1<float, float, false, false>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)d, n, s,
+                                       m, nullptr, ra, rb, rc, rd, (float*)nullptr, (float*)nullptr,
+                                       (float*)nullptr);
+  else
+    stage1<double, float, false, false>(ctx, (const double*)a, (const double*)b, (const double*)c,
+                                        (const double*)d, n, s, m, nullptr, ra, rb, rc, rd, (float*)nullptr,
+                                        (float*)nullptr, (float*)nullptr);
+}
+
+}  // namespace tdp

@@ -1,0 +1,116 @@
+// Tile staging between HBM and shared memory for the per-thread sub-system
+// kernels.  A CTA of T threads owns T consecutive blocks (sub-systems) whose
+// rows are contiguous in memory.  Global rows are read and written with
+// coalesced 16-byte vectors; in shared memory row j of the block owned by
+// thread t sits at index j * ld + t with ld = T + 1 (odd), so that the
+// per-thread sequential sweeps read consecutive words across a warp.
+#pragma once
+#include "tdp_device.cuh"
+
+namespace tdp {
+
+struct TileGeom {
+  int64_t ts;             // first global row of the tile
+  int64_t te;             // one past the last global row
+  int s;                  // nominal rows per block
+  unsigned magic;         // ceil(2^32 / s): p / s == __umulhi(p, magic) while p * s < 2^32
+  int ld;                 // shared-memory leading dimension (T + 1)
+  const uint32_t* own;    // mapped tiles: owner (t << 16 | j) of every tile row
+};
+
+template <bool MAPPED>
+__device__ __forceinline__ void owner(const TileGeom& g, int p, int& t, int& j) {
+  if constexpr (MAPPED) {
+    const uint32_t o = g.own[p];
+    t = int(o >> 16);
+    j = int(o & 0xffffu);
+  } else {
+    t = int(__umulhi(unsigned(p), g.magic));
+    j = p - t * g.s;
+  }
+}
+
+// Load NA arrays of storage type S (n_arr valid elements each) for rows
+// [ts, te) into shared tiles of compute type C.
+template <typename S, typename C, bool MAPPED, int NA>
+__device__ __forceinline__ void tile_load(const TileGeom& g, const S* const* src, C* const* dst, int64_t n_arr) {
+  constexpr int V = Vec<S>::W;
+  constexpr int U = 2;  // chunks in flight per thread per iteration
+  const int64_t q0 = g.ts / V, q1 = (g.te + V - 1) / V;
+  const int64_t step = blockDim.x;
+  for (int64_t qb = q0 + threadIdx.x; qb < q1; qb += U * step) {
+    Vec<S> v[U][NA];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = qb + u * step;
+      const int64_t base = q * V;
+      if (q < q1 && base + V <= n_arr) {
+#pragma unroll
+        for (int i = 0; i < NA; ++i) v[u][i] = ldg16<S>(src[i] + base);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NA; ++i)
+#pragma unroll
+          for (int e = 0; e < V; ++e) v[u][i].v[e] = (q < q1 && base + e < n_arr) ? src[i][base + e] : S(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = qb + u * step;
+      if (q >= q1) continue;
+      const int64_t base = q * V;
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int64_t pg = base + e;
+        if (pg < g.ts || pg >= g.te) continue;
+        int t, j;
+        owner<MAPPED>(g, int(pg - g.ts), t, j);
+        const int idx = j * g.ld + t;
+#pragma unroll
+        for (int i = 0; i < NA; ++i) dst[i][idx] = cvt<C>(v[u][i].v[e]);
+      }
+    }
+  }
+}
+
+// Store NA shared tiles of type C to global arrays of type D for rows
+// [ts, te).  Vectors that straddle the tile edge are written element by
+// element so that neighbouring tiles are never touched.
+template <typename C, typename D, bool MAPPED, int NA>
+__device__ __forceinline__ void tile_store(const TileGeom& g, const C* const* src, D* const* dst) {
+  constexpr int V = Vec<D>::W;
+  const int64_t q0 = g.ts / V, q1 = (g.te + V - 1) / V;
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int64_t base = q * V;
+    Vec<D> v[NA];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int64_t pg = base + e;
+      if (pg < g.ts || pg >= g.te) continue;
+      int t, j;
+      owner<MAPPED>(g, int(pg - g.ts), t, j);
+      const int idx = j * g.ld + t;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) v[i].v[e] = cvt<D>(src[i][idx]);
+    }
+    if (base >= g.ts && base + V <= g.te) {
+#pragma unroll
+      for (int i = 0; i < NA; ++i) stg16<D>(dst[i] + base, v[i]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int64_t pg = base + e;
+        if (pg < g.ts || pg >= g.te) continue;
+#pragma unroll
+        for (int i = 0; i < NA; ++i) dst[i][pg] = v[i].v[e];
+      }
+    }
+  }
+}
+
+// Fill the owner table of a mapped tile (thread t writes its block's rows).
+__device__ __forceinline__ void fill_owner(uint32_t* own, int t, int p0, int len) {
+  for (int j = 0; j < len; ++j) own[p0 + j] = (uint32_t(t) << 16) | uint32_t(j);
+}
+
+}  // namespace tdp

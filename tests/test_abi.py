@@ -1,0 +1,85 @@
+"""The C ABI library on the host: it loads, exports every declared symbol,
+and rejects bad arguments before touching a device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tdp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tdp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2510_27351_gb300 as tdp
+
+    lib = ctypes.CDLL(tdp._build.LIB)
+    names = _declared()
+    assert "tdp_solve" in names and "tdp_predict_s" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(tdp.SYMBOLS) == names
+
+
+def test_bad_arguments_rejected_on_host():
+    import paper_2510_27351_gb300 as tdp
+
+    lib = tdp.LIB
+    # n < 1
+    assert lib.tdp_solve(16, 16, 16, 16, 16, 0, 4, 0, 0, 0) == 1
+    assert "n must be" in tdp.tdp_last_error()
+    # s out of range
+    assert lib.tdp_solve(16, 16, 16, 16, 16, 10, 1, 0, 0, 0) == 1
+    assert lib.tdp_solve(16, 16, 16, 16, 16, 10, 2000, 0, 0, 0) == 1
+    # null and misaligned pointers
+    assert lib.tdp_solve(0, 16, 16, 16, 16, 10, 4, 0, 0, 0) == 1
+    assert "null" in tdp.tdp_last_error()
+    assert lib.tdp_solve(24, 16, 16, 16, 16, 10, 4, 0, 0, 0) == 1
+    assert "aligned" in tdp.tdp_last_error()
+    # bad dtype and refinement count
+    assert lib.tdp_solve(16, 16, 16, 16, 16, 10, 4, 7, 0, 0) == 1
+    assert lib.tdp_solve(16, 16, 16, 16, 16, 10, 4, 2, 9, 0) == 1
+    # batched: batch < 1, null offsets
+    assert lib.tdp_solve_batched(16, 0, 10, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
+    assert lib.tdp_solve_batched(0, 1, 10, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
+    # strided: bad strides
+    assert lib.tdp_solve_strided(2, 8, -1, 1, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
+    # backward refuses the refinement dtype
+    assert lib.tdp_solve_backward(16, 1, 8, 16, 16, 16, 16, 16, 0, 0, 0, 0, 4, 2, 0) == 1
+
+
+def test_predictor_is_host_only_and_valid():
+    import paper_2510_27351_gb300 as tdp
+
+    for n in (1, 64, 4500, 65536, 1 << 20, 1 << 26):
+        for dt in (0, 1, 2):
+            s = tdp.tdp_predict_s(n, 1, dt)
+            assert 2 <= s <= 1024
+
+
+def test_predictor_table_loading(tmp_path):
+    import paper_2510_27351_gb300 as tdp
+
+    p = tmp_path / "t.txt"
+    p.write_text("# dtype n batch s\n0 1024 1 8\n0 1048576 1 64\n0 1048576 4096 16\n")
+    tdp.tdp_load_table(str(p))
+    try:
+        assert tdp.tdp_predict_s(1000, 1, 0) == 8
+        assert tdp.tdp_predict_s(1 << 21, 1, 0) == 64
+        assert tdp.tdp_predict_s(1 << 20, 4000, 0) == 16
+        # equal distance in log2 N: the larger s wins
+        assert tdp.tdp_predict_s(32768, 1, 0) == 64
+        bad = tmp_path / "bad.txt"
+        bad.write_text("0 1024 1 1\n")
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_load_table(str(bad))
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_load_table(str(tmp_path / "missing.txt"))
+        assert tdp.tdp_predict_s(1000, 1, 0) == 8  # unchanged by the failed loads
+    finally:
+        tdp.tdp_load_table("")
