@@ -262,7 +262,7 @@ def run_ours(args, world, rank, local):
 
     # ---- roofline of the dominant kernel (library event timing of the same step) ----
     prof = profile_kernels(tdp, step_f64, max(3, min(args.steps, 10)))
-    dom = max(prof.items(), key=lambda kv: kv[1][0] * kv[1][1])
+    dom = max(prof.items(), key=lambda kv: kv[1][0] * kv[1][1])  # largest total time per step
     st1 = prof.get("stage1_keep_f64")
     roof = None
     if st1:

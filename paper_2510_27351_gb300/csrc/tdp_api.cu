@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -63,6 +64,21 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
   return &g_ws[{dev, st}];
 }
 
+// Launch knobs for experiments: TDP_PIPELINE=1 selects the warp-tile cp.async
+// pipeline (and the fused refinement pass), TDP_S_REC the sub-system size inside the interface recursion,
+// TDP_SMEM_BUDGET the shared memory per CTA of the non-pipelined kernels.
+void tune_from_env(Ctx& ctx) {
+  if (const char* v = std::getenv("TDP_PIPELINE")) ctx.pipeline = std::atoi(v) != 0;
+  if (const char* v = std::getenv("TDP_S_REC")) {
+    const int r = std::atoi(v);
+    if (r >= 3 && r <= 1024) ctx.s_rec = r;
+  }
+  if (const char* v = std::getenv("TDP_SMEM_BUDGET")) {
+    const int r = std::atoi(v);
+    if (r >= 4096 && r <= 227 * 1024) ctx.smem_budget = r;
+  }
+}
+
 // Run a driver twice: a dry run that sizes the workspace, then the real one.
 template <typename F>
 int run(void* stream, const char* fn, F&& driver) {
@@ -71,6 +87,7 @@ int run(void* stream, const char* fn, F&& driver) {
   Workspace* ws = workspace_for(st, &dev);
   Arena sizing;
   Ctx dry;
+  tune_from_env(dry);
   dry.stream = st;
   dry.ar = &sizing;
   dry.dry = true;
@@ -108,6 +125,7 @@ int run(void* stream, const char* fn, F&& driver) {
   arena.base = ws->buf;
   arena.cap = ws->cap;
   Ctx ctx;
+  tune_from_env(ctx);
   ctx.stream = st;
   ctx.status = ws->status;
   ctx.ar = &arena;

@@ -35,6 +35,7 @@ struct Ctx {
   cudaError_t err = cudaSuccess;
   int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
   int s_rec = 32;              // sub-system size inside the interface-system recursion
+  bool pipeline = false;       // warp-tile cp.async pipeline (TDP_PIPELINE=1); slower on GB300 so far
   std::string msg;
   void fail(cudaError_t e, const char* where) {
     if (err == cudaSuccess && e != cudaSuccess) {

@@ -39,47 +39,48 @@ __device__ __forceinline__ void write_iface(int64_t k, const IfaceRows& r, doubl
 // when KEEP is set (rows L and R get the values that make Stage 3's formula
 // return the interface values).  Arithmetic in C.
 // ---------------------------------------------------------------------------
-template <typename C, bool KEEP>
-__device__ __forceinline__ IfaceRows block_reduce(C* sA, C* sB, C* sC, C* sD, int ld, const BlockInfo& bi,
+template <typename S, typename C, bool KEEP>
+__device__ __forceinline__ IfaceRows block_reduce(S* sA, S* sB, S* sC, S* sD, int ld, const BlockInfo& bi,
                                                   unsigned* status) {
+  // tiles hold type S; arithmetic in C; values written back are exact in S
   IfaceRows out;
   const int len = bi.len;
   if (len <= 0) {
     out = IfaceRows{0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0};
     return out;
   }
-  C a0 = sA[0], b0 = sB[0], c0 = sC[0], d0 = sD[0];
+  C a0 = cvt<C>(sA[0]), b0 = cvt<C>(sB[0]), c0 = cvt<C>(sC[0]), d0 = cvt<C>(sD[0]);
   if (bi.first) a0 = C(0);
   if (len == 1) {
     if (bi.last) c0 = C(0);
     out = IfaceRows{to_f64(a0), to_f64(b0), to_f64(c0), to_f64(d0), 0.0, 1.0, 0.0, 0.0};
-    if (KEEP) { sA[0] = C(-1); sC[0] = C(0); sD[0] = C(0); }
+    if (KEEP) { sA[0] = S(-1); sC[0] = S(0); sD[0] = S(0); }
     return out;
   }
   // forward sweep, rows 1..len-1
   C gam, del, alp;
   {
-    const C a1 = sA[ld], b1 = sB[ld];
-    C c1 = sC[ld];
-    const C d1 = sD[ld];
+    const C a1 = cvt<C>(sA[ld]), b1 = cvt<C>(sB[ld]);
+    C c1 = cvt<C>(sC[ld]);
+    const C d1 = cvt<C>(sD[ld]);
     if (len == 2 && bi.last) c1 = C(0);
     const C r = rcp(b1, status);
     gam = c1 * r;
     del = d1 * r;
     alp = a1 * r;
-    sA[ld] = alp; sC[ld] = gam; sD[ld] = del;
+    sA[ld] = cvt<S>(alp); sC[ld] = cvt<S>(gam); sD[ld] = cvt<S>(del);
   }
   for (int j = 2; j < len; ++j) {
-    const C aj = sA[j * ld], bj = sB[j * ld];
-    C cj = sC[j * ld];
-    const C dj = sD[j * ld];
+    const C aj = cvt<C>(sA[j * ld]), bj = cvt<C>(sB[j * ld]);
+    C cj = cvt<C>(sC[j * ld]);
+    const C dj = cvt<C>(sD[j * ld]);
     if (j == len - 1 && bi.last) cj = C(0);
     const C r = rcp(fma(-aj, gam, bj), status);
     const C q = aj * r;
     gam = cj * r;
     del = fma(-q, del, dj * r);
     alp = -q * alp;
-    sA[j * ld] = alp; sC[j * ld] = gam; sD[j * ld] = del;
+    sA[j * ld] = cvt<S>(alp); sC[j * ld] = cvt<S>(gam); sD[j * ld] = cvt<S>(del);
   }
   out.a1 = to_f64(alp);
   out.b1 = 1.0;
@@ -90,13 +91,13 @@ __device__ __forceinline__ IfaceRows block_reduce(C* sA, C* sB, C* sC, C* sD, in
   if (len == 2) {
     ap = C(0); gp = C(-1); dp = C(0);  // x[L+1] is x[R] itself
   } else {
-    ap = sA[(len - 2) * ld]; gp = sC[(len - 2) * ld]; dp = sD[(len - 2) * ld];
+    ap = cvt<C>(sA[(len - 2) * ld]); gp = cvt<C>(sC[(len - 2) * ld]); dp = cvt<C>(sD[(len - 2) * ld]);
     for (int j = len - 3; j >= 1; --j) {
-      const C aj = sA[j * ld], gj = sC[j * ld], dj = sD[j * ld];
+      const C aj = cvt<C>(sA[j * ld]), gj = cvt<C>(sC[j * ld]), dj = cvt<C>(sD[j * ld]);
       dp = fma(-gj, dp, dj);
       ap = fma(-gj, ap, aj);
       gp = -gj * gp;
-      if (KEEP) { sA[j * ld] = ap; sC[j * ld] = gp; sD[j * ld] = dp; }
+      if (KEEP) { sA[j * ld] = cvt<S>(ap); sC[j * ld] = cvt<S>(gp); sD[j * ld] = cvt<S>(dp); }
     }
   }
   out.a0 = to_f64(a0);
@@ -104,42 +105,43 @@ __device__ __forceinline__ IfaceRows block_reduce(C* sA, C* sB, C* sC, C* sD, in
   out.c0 = to_f64(-c0 * gp);
   out.d0 = to_f64(fma(-c0, dp, d0));
   if (KEEP) {
-    sA[0] = C(-1); sC[0] = C(0); sD[0] = C(0);
-    sA[(len - 1) * ld] = C(0); sC[(len - 1) * ld] = C(-1); sD[(len - 1) * ld] = C(0);
+    sA[0] = S(-1); sC[0] = S(0); sD[0] = S(0);
+    sA[(len - 1) * ld] = S(0); sC[(len - 1) * ld] = S(-1); sD[(len - 1) * ld] = S(0);
   }
   return out;
 }
 
 // Interior solve of one block with x[L] = yl and x[R] = yr known (Stage 3,
 // the "substitute and solve the rest" step).  Reads a, b, c, d from the
-// tiles, leaves x in the D tile, uses the C tile as scratch.
-template <typename C>
-__device__ __forceinline__ void block_substitute(C* sA, C* sB, C* sC, C* sD, int ld, int len, C yl, C yr,
+// tiles (type S), leaves x in the D tile, uses the C tile as scratch.
+template <typename S, typename C>
+__device__ __forceinline__ void block_substitute(S* sA, S* sB, S* sC, S* sD, int ld, int len, C yl, C yr,
                                                  unsigned* status) {
   if (len <= 0) return;
-  if (len == 1) { sD[0] = yl; return; }
-  if (len == 2) { sD[0] = yl; sD[ld] = yr; return; }
+  if (len == 1) { sD[0] = cvt<S>(yl); return; }
+  if (len == 2) { sD[0] = cvt<S>(yl); sD[ld] = cvt<S>(yr); return; }
   // interior rows 1..len-2
   C gam = C(0), del = C(0);
   for (int j = 1; j <= len - 2; ++j) {
-    const C aj = sA[j * ld], bj = sB[j * ld], cj = sC[j * ld];
-    C dj = sD[j * ld];
+    const C aj = cvt<C>(sA[j * ld]), bj = cvt<C>(sB[j * ld]), cj = cvt<C>(sC[j * ld]);
+    C dj = cvt<C>(sD[j * ld]);
     if (j == 1) dj = fma(-aj, yl, dj);
     if (j == len - 2) dj = fma(-cj, yr, dj);
     const C den = (j == 1) ? bj : fma(-aj, gam, bj);
     const C r = rcp(den, status);
     del = (j == 1) ? dj * r : fma(-aj * r, del, dj * r);
     gam = (j == len - 2) ? C(0) : cj * r;
-    sC[j * ld] = gam;
-    sD[j * ld] = del;
+    sC[j * ld] = cvt<S>(gam);
+    sD[j * ld] = cvt<S>(del);
   }
   C xn = del;  // x at row len-2
+  sD[(len - 2) * ld] = cvt<S>(xn);
   for (int j = len - 3; j >= 1; --j) {
-    xn = fma(-sC[j * ld], xn, sD[j * ld]);
-    sD[j * ld] = xn;
+    xn = fma(-cvt<C>(sC[j * ld]), xn, cvt<C>(sD[j * ld]));
+    sD[j * ld] = cvt<S>(xn);
   }
-  sD[0] = yl;
-  sD[(len - 1) * ld] = yr;
+  sD[0] = cvt<S>(yl);
+  sD[(len - 1) * ld] = cvt<S>(yr);
 }
 
 // ---------------------------------------------------------------------------
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) k_stage1(const S* __restrict__ a, const S
   }
   __syncthreads();
   if (t < nb) {
-    const IfaceRows r = block_reduce<C, KEEP>(sA + t, sB + t, sC + t, sD + t, ld, bi, status);
+    const IfaceRows r = block_reduce<C, C, KEEP>(sA + t, sB + t, sC + t, sD + t, ld, bi, status);
     write_iface(k0 + t, r, ra, rb, rc, rd);
   }
   if constexpr (KEEP) {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(256) k_stage3_resolve(const S* __restrict__ a,
   __syncthreads();
   if (t < nb) {
     const double2 v = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));
-    block_substitute<C>(sA + t, sB + t, sC + t, sD + t, ld, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
+    block_substitute<C, C>(sA + t, sB + t, sC + t, sD + t, ld, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
   }
   __syncthreads();
   {

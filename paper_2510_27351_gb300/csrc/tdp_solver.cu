@@ -2,12 +2,14 @@
 // stages of the partition method (Sec. I), for single, batched, strided and
 // transposed (adjoint) solves.
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
 
 #include "tdp_internal.h"
-#include "tdp_kernels.cuh"
+#include "tdp_pipe.cuh"
 
 namespace tdp {
 
@@ -58,18 +60,127 @@ const char* tname(const char* f64, const char* f32) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-tile pipeline geometry
+// ---------------------------------------------------------------------------
+int sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!count[dev]) cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev);
+  return count[dev] > 0 ? count[dev] : 1;
+}
+
+// Leading dimension of a warp tile: the smallest ld >= 32 whose element-copy
+// pattern (lane l copies tile row base + l, row p -> lane p / s, slot p % s)
+// needs the fewest shared-memory wavefronts, simulated bank by bank.
+int pick_ld(int s, int el) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> memo;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = memo.find({s, el});
+  if (it != memo.end()) return it->second;
+  int best = 1 << 30, best_ld = 33;
+  for (int ld = 32; ld < 32 + 64; ++ld) {
+    int worst = 0;
+    for (int base = 0; base < 32 * s; base += 32) {
+      int cost = 0;
+      const int group = (el == 8) ? 16 : 32;  // lanes served per 128-byte wavefront
+      for (int g0 = 0; g0 < 32; g0 += group) {
+        int hits[32] = {0};
+        int mx = 0;
+        for (int l = g0; l < g0 + group; ++l) {
+          const int p = base + l;
+          if (p >= 32 * s) continue;
+          const int t = p / s, j = p % s;
+          const int word = (j * ld + t) % group;
+          mx = std::max(mx, ++hits[word]);
+        }
+        cost += mx;
+      }
+      worst = std::max(worst, cost);
+    }
+    if (worst < best) {
+      best = worst;
+      best_ld = ld;
+    }
+  }
+  memo[{s, el}] = best_ld;
+  return best_ld;
+}
+
+size_t warp_bytes(int s, int ld, int el, bool mapped, int arrays) {
+  size_t b = size_t(arrays) * s * ld * el;
+  b = (b + 15) & ~size_t(15);
+  const size_t o = mapped ? size_t(32) * s * 4 : 0;
+  return 2 * (b + o);
+}
+
+constexpr size_t kPipeWarpMax = 113 * 1024;  // at least two warps per SM
+
+// Warps per CTA of the pipelined kernels (each warp has its own buffers, so
+// this only changes how the resident warps are grouped into CTAs).
+int pipe_warps() {
+  static int w = [] {
+    const char* v = std::getenv("TDP_PIPE_WARPS");
+    const int r = v ? std::atoi(v) : 1;
+    return (r >= 1 && r <= 4) ? r : 1;
+  }();
+  return w;
+}
+
+struct PipeCfg {
+  bool ok = false;
+  int ld = 33, warps = 1, grid = 1;
+  size_t smem = 0;
+};
+
+template <typename K>
+PipeCfg pipe_cfg(K kern, int s, int el, bool mapped, int64_t m, int arrays = 4) {
+  PipeCfg c;
+  c.ld = pick_ld(s, el);
+  const size_t per = warp_bytes(s, c.ld, el, mapped, arrays);
+  if (per > kPipeWarpMax) return c;
+  c.warps = int(std::min<size_t>(size_t(pipe_warps()), size_t(kMaxSmem) / per));
+  c.smem = per * c.warps;
+  allow_smem(kern);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * c.warps, c.smem) != cudaSuccess ||
+      per_sm < 1)
+    return c;
+  const int64_t tiles = (m + 31) / 32;
+  const int64_t want = (tiles + c.warps - 1) / c.warps;
+  c.grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(per_sm) * sm_count())));
+  c.ok = true;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename S, typename C, bool MAPPED, bool KEEP>
 void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
-            const int64_t* blk, double* ra, double* rb, double* rc, double* rd, C* ka, C* kg, C* kd) {
+            const int64_t* blk, double* ra, double* rb, double* rc, double* rd, C* ka, C* kg, C* kd,
+            const char* name = nullptr) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  const char* nm = name ? name : KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32");
+  if (ctx.pipeline) {
+    auto pk = k_stage1_pipe<S, C, MAPPED, KEEP>;
+    const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
+    if (pc.ok) {
+      pre_launch(ctx, nm);
+      pk<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(a, b, c, d, n, s, pc.ld, magic_for(s), m, blk, ra, rb,
+                                                           rc, rd, ka, kg, kd, ctx.status);
+      post_launch(ctx, "stage 1");
+      return;
+    }
+  }
   size_t smem;
   const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
   auto kern = k_stage1<S, C, MAPPED, KEEP>;
   allow_smem(kern);
   const int64_t grid = (m + T - 1) / T;
-  pre_launch(ctx, KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32"));
+  pre_launch(ctx, nm);
   kern<<<unsigned(grid), T, smem, ctx.stream>>>(a, b, c, d, n, s, magic_for(s), m, blk, ra, rb, rc, rd, ka, kg,
                                                 kd, ctx.status);
   post_launch(ctx, "stage 1");
@@ -77,7 +188,7 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
 
 template <typename C, typename S, bool MAPPED>
 void stage3_kept(Ctx& ctx, const C* ka, const C* kg, const C* kd, int64_t n, int s, int64_t m, const int64_t* blk,
-                 const double* y, S* x) {
+                 const double* y, S* x, const char* name = nullptr) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
   size_t smem;
   const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);  // same tiling as Stage 1
@@ -85,7 +196,7 @@ void stage3_kept(Ctx& ctx, const C* ka, const C* kg, const C* kd, int64_t n, int
   auto kern = k_stage3_kept<C, S, MAPPED>;
   allow_smem(kern);
   const int64_t grid = (m + T - 1) / T;
-  pre_launch(ctx, "stage3_kept_f64");
+  pre_launch(ctx, name ? name : "stage3_kept_f64");
   kern<<<unsigned(grid), T, need, ctx.stream>>>(ka, kg, kd, n, s, magic_for(s), m, blk, y, x);
   post_launch(ctx, "stage 3");
 }
@@ -94,6 +205,17 @@ template <typename S, typename C, bool MAPPED>
 void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
                     const int64_t* blk, const double* y, S* x) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  if (ctx.pipeline) {
+    auto pk = k_stage3_resolve_pipe<S, C, MAPPED>;
+    const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
+    if (pc.ok) {
+      pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
+      pk<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(a, b, c, d, n, s, pc.ld, magic_for(s), m, blk, y, x,
+                                                           ctx.status);
+      post_launch(ctx, "stage 3");
+      return;
+    }
+  }
   size_t smem;
   const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
   auto kern = k_stage3_resolve<S, C, MAPPED>;
@@ -131,9 +253,10 @@ void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double*
   double* rc2 = ctx.ar->take<double>(2 * m2);
   double* rd2 = ctx.ar->take<double>(2 * m2);
   double* y2 = ctx.ar->take<double>(2 * m2);
-  stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd);
+  stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd,
+                                      "iface_stage1_f64");
   solve_interface(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
-  stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y);
+  stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f64");
 }
 
 // ---------------------------------------------------------------------------
@@ -305,6 +428,47 @@ unsigned grid_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------------------
+// Refinement with the fused pass (k_refine_pass): Stage 1 in binary32, then
+// per correction one pass that finishes the previous correction, updates x
+// in binary64 and prepares the next interface right-hand side.  HBM traffic
+// for q corrections: 4 + 5 + 6q words per row.  Returns false (and queues
+// nothing) when the warp tile does not fit in shared memory.
+// ---------------------------------------------------------------------------
+template <bool MAPPED>
+bool refine_fused(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
+                  int64_t m, const int64_t* blk, double* ra, double* rb, double* rc, double* rd, double* y,
+                  int iters) {
+  if (!ctx.pipeline) return false;
+  const size_t per = warp_bytes(s, pick_ld(s, 8), 8, MAPPED, 6);
+  if (per > kPipeWarpMax) return false;
+  const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
+  double* rd2 = ctx.ar->take<double>(iters > 0 ? 2 * m : 1);
+  double* xb[2] = {ctx.ar->take<double>(iters > 0 ? n : 1), ctx.ar->take<double>(iters > 1 ? n : 1)};
+  stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                       (float*)nullptr, (float*)nullptr);
+  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+  for (int it = 0; it <= iters; ++it) {
+    const double* xin = it == 0 ? nullptr : xb[(it - 1) & 1];
+    double* xo = it == iters ? (double*)x : xb[it & 1];
+    double* rdn = it < iters ? rd2 : nullptr;
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      auto kern = it == 0 ? k_refine_pass<MAPPED, false> : k_refine_pass<MAPPED, true>;
+      const PipeCfg pc = pipe_cfg(kern, s, 8, MAPPED, m, 6);
+      if (!pc.ok) {
+        ctx.fail(cudaErrorInvalidConfiguration, "refine pass configuration");
+        return true;
+      }
+      pre_launch(ctx, "refine_pass");
+      kern<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(A, B, Cc, D, xin, n, s, pc.ld, magic_for(s), m, blk, y,
+                                                             xo, rdn, ctx.status);
+      post_launch(ctx, "refine pass");
+    }
+    if (it < iters) solve_interface(ctx, ra, rb, rc, rd2, y, 2 * m);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // One solve over blocks given either arithmetically (one system) or by blk.
 // ---------------------------------------------------------------------------
 template <bool MAPPED>
@@ -331,8 +495,10 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
                                 (T*)nullptr);
     solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
     stage3_resolve<T, T, MAPPED>(ctx, A, B, Cc, D, n, s, m, blk, y, (T*)x);
+  } else if (refine_fused<MAPPED>(ctx, a, b, c, d, x, n, s, m, blk, ra, rb, rc, rd, y, refine_iters)) {
+    // binary32 eliminations, binary64 residual and correction, one fused pass per correction
   } else {
-    // binary32 eliminations, binary64 residual and correction
+    // binary32 eliminations, binary64 residual and correction (separate kernels)
     const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
     double* X = (double*)x;
     double* r = ctx.ar->take<double>(refine_iters > 0 ? n : 1);

@@ -35,7 +35,7 @@ __device__ __forceinline__ void owner(const TileGeom& g, int p, int& t, int& j) 
 template <typename S, typename C, bool MAPPED, int NA>
 __device__ __forceinline__ void tile_load(const TileGeom& g, const S* const* src, C* const* dst, int64_t n_arr) {
   constexpr int V = Vec<S>::W;
-  constexpr int U = 2;  // chunks in flight per thread per iteration
+  constexpr int U = 4;  // chunks in flight per thread per iteration
   const int64_t q0 = g.ts / V, q1 = (g.te + V - 1) / V;
   const int64_t step = blockDim.x;
   for (int64_t qb = q0 + threadIdx.x; qb < q1; qb += U * step) {
