@@ -163,6 +163,32 @@ int tdp_thomas_batched(const int64_t* offsets, int32_t batch, int64_t total_n, c
 int tdp_stage1(const void* a, const void* b, const void* c, const void* d, int64_t n, int32_t s, tdp_dtype dtype,
                double* ra, double* rb, double* rc, double* rd, void* stream);
 
+/* Allocation-free solve of one system (the paper has no counterpart; this
+ * is a service of the library).  For callers that cannot allocate device
+ * memory when they solve: code running while a stream is captured into a
+ * CUDA graph (cudaMalloc is not permitted there), latency-critical loops in
+ * which an allocation would synchronise the device, and hosts whose memory
+ * pool owns all device memory.
+ *
+ * Same arguments and results as tdp_solve, for TDP_F64 and TDP_F32 only (no
+ * refinement).  Scratch comes from one statically sized 16 MiB __device__
+ * array inside the library, present on every GPU that loads the library
+ * until the process exits; the call makes no cudaMalloc, cudaFree or other
+ * device allocation.  Binary64 solves re-solve the interiors in Stage 3
+ * instead of keeping per-row coefficients, so only the interface systems use
+ * scratch: about 4.3 bytes per unknown at s = 32, i.e. n up to about 3.9
+ * million unknowns at s = 32 (more with larger s).  Larger sizes are
+ * rejected with TDP_EINVAL and a message giving the bytes needed.
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the previous call's contents (the status word is cleared at the start of
+ * each call): calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller. */
+int tdp_solve_noalloc(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
+                      tdp_dtype dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_profile_enable.restype = None
     lib.tdp_profile_summary.argtypes = [ctypes.c_char_p, I64]
     lib.tdp_profile_summary.restype = I64
+    lib.tdp_solve_noalloc.argtypes = [P, P, P, P, P, I64, I32, I32, P]
     return lib
 
 
@@ -65,7 +66,8 @@ LIB = _load()
 # Every symbol the header declares (checked by the tests).
 SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_backward", "tdp_predict_s",
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
-           "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary")
+           "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
+           "tdp_solve_noalloc")
 
 
 def _check(rc: int):
@@ -107,6 +109,12 @@ def _dtype_code(t: torch.Tensor, refine: bool) -> int:
 def tdp_solve(a, b, c, d, x, n, s, dtype, refine_iters=0, stream=None):
     _check(LIB.tdp_solve(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), int(n), int(s), int(dtype),
                          int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_noalloc(a, b, c, d, x, n, s, dtype, stream=None):
+    """Allocation-free single-system solve (static 16 MiB device scratch)."""
+    _check(LIB.tdp_solve_noalloc(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), int(n), int(s), int(dtype),
+                                 _stream(stream)))
 
 
 def tdp_solve_batched(offsets, batch, total_n, a, b, c, d, x, s, dtype, refine_iters=0, stream=None):

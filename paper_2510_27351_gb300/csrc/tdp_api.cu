@@ -183,6 +183,9 @@ int interval_rule(double n) {
 
 }  // namespace
 
+int set_last_error(int code, const std::string& msg) { return set_error(code, msg); }
+bool checked_mode() { return g_checked.load() != 0; }
+
 // ---------------------------------------------------------------------------
 // Launch counting and event-based per-kernel timing.
 // ---------------------------------------------------------------------------
@@ -198,10 +201,10 @@ thread_local cudaEvent_t t_open = nullptr;
 thread_local const char* t_open_name = nullptr;
 }  // namespace
 
-void launch_begin(cudaStream_t st, const char* name) {
+void launch_begin(cudaStream_t st, const char* name, bool events_ok) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   t_open = nullptr;
-  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  if (!events_ok || !g_prof_on.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
   cudaEvent_t e0;

@@ -36,6 +36,7 @@ struct Ctx {
   int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
   int s_rec = 32;              // sub-system size inside the interface-system recursion
   bool pipeline = false;       // warp-tile cp.async pipeline (TDP_PIPELINE=1); slower on GB300 so far
+  bool events_ok = true;       // the profiler may create CUDA events around launches
   std::string msg;
   void fail(cudaError_t e, const char* where) {
     if (err == cudaSuccess && e != cudaSuccess) {
@@ -47,7 +48,7 @@ struct Ctx {
 
 // Launch bookkeeping: counts every kernel launch and, when profiling is on,
 // brackets it with CUDA events on the launch stream (tdp_profile_*).
-void launch_begin(cudaStream_t st, const char* name);
+void launch_begin(cudaStream_t st, const char* name, bool events_ok = true);
 void launch_end(cudaStream_t st);
 
 // Drivers.  Every pointer is a device pointer; all work is queued on ctx.stream.
@@ -62,8 +63,16 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
                     void* gd, int s, tdp_dtype dt);
 void thomas_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
                     const void* b, const void* c, const void* d, void* x, tdp_dtype dt);
+// Single-system solve whose scratch is only the interface systems (binary64
+// re-solves the interiors in Stage 3 instead of keeping coefficients).
+void solve_single_lean(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                       int s, tdp_dtype dt);
 void stage1_only(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, int64_t n, int s,
                  tdp_dtype dt, double* ra, double* rb, double* rc, double* rd);
+
+// Error message of the calling host thread (tdp_last_error) and checked mode.
+int set_last_error(int code, const std::string& msg);
+bool checked_mode();
 
 // Predictor (host 1-NN over the loaded table; tdp_api.cu).
 int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);

@@ -47,7 +47,7 @@ int pick_threads(const Ctx& ctx, int s, int arrays, int elem, bool mapped, size_
   return T;
 }
 
-void pre_launch(Ctx& ctx, const char* what) { launch_begin(ctx.stream, what); }
+void pre_launch(Ctx& ctx, const char* what) { launch_begin(ctx.stream, what, ctx.events_ok); }
 
 void post_launch(Ctx& ctx, const char* what) {
   launch_end(ctx.stream);
@@ -675,6 +675,32 @@ void thomas_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
                                                            (const double*)d, (double*)x, offsets, batch, 0, 0, 1,
                                                            total_n, (double*)scratch, ctx.status);
   post_launch(ctx, "thomas");
+}
+
+void solve_single_lean(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                       int s, tdp_dtype dt) {
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  const int64_t m = (n + s - 1) / s;
+  double* ra = ctx.ar->take<double>(2 * m);
+  double* rb = ctx.ar->take<double>(2 * m);
+  double* rc = ctx.ar->take<double>(2 * m);
+  double* rd = ctx.ar->take<double>(2 * m);
+  double* y = ctx.ar->take<double>(2 * m);
+  if (dt == TDP_F64) {
+    using T = double;
+    const T *A = (const T*)a, *B = (const T*)b, *Cc = (const T*)c, *D = (const T*)d;
+    stage1<T, T, false, false>(ctx, A, B, Cc, D, n, s, m, nullptr, ra, rb, rc, rd, (T*)nullptr, (T*)nullptr,
+                               (T*)nullptr);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    stage3_resolve<T, T, false>(ctx, A, B, Cc, D, n, s, m, nullptr, y, (T*)x);
+  } else {
+    using T = float;
+    const T *A = (const T*)a, *B = (const T*)b, *Cc = (const T*)c, *D = (const T*)d;
+    stage1<T, T, false, false>(ctx, A, B, Cc, D, n, s, m, nullptr, ra, rb, rc, rd, (T*)nullptr, (T*)nullptr,
+                               (T*)nullptr);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    stage3_resolve<T, T, false>(ctx, A, B, Cc, D, n, s, m, nullptr, y, (T*)x);
+  }
 }
 
 void stage1_only(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, int64_t n, int s,
