@@ -75,8 +75,10 @@ int tdp_solve(const void* a, const void* b, const void* c, const void* d, void* 
  *  total_n    : offsets[batch] (passed by value so that no copy to the host is
  *               needed; the device checks it and reports TDP_EINVAL through
  *               the status word when it disagrees).
- *  s          : sub-system size for every system (2..1024), or 0 to use the
- *               tuned per-size table (tdp_predict_s per system).
+ *  s          : sub-system size for every system (2..1024), or 0 to choose
+ *               one per system on the device with the size model
+ *               (tdp_predict_s_batched), capped at the largest size the
+ *               model gives for the nearest batch size in its table.
  * Empty systems are allowed.  Other arguments as tdp_solve. */
 int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                       const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
@@ -114,6 +116,13 @@ int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, c
  * paper's interval rule (Sec. II-D).  Never fails: returns a valid s >= 2. */
 int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype);
 
+/* The same size model evaluated on the device, one system per thread: s_out[j]
+ * (DEVICE array of batch int32) receives the predicted s of system j of
+ * the batch described by the DEVICE offsets (batch+1 int64), with the batch
+ * size as second feature.  This inference kernel is what tdp_solve_batched
+ * runs when called with s = 0.  Asynchronous on `stream`. */
+int tdp_predict_s_batched(const int64_t* offsets, int32_t batch, tdp_dtype dtype, int32_t* s_out, void* stream);
+
 /* Replace the predictor's table (text: lines "dtype n batch s", '#' comments;
  * dtype 0/1/2 as tdp_dtype); an empty path "" restores the built-in table.
  * Returns TDP_OK or TDP_EINVAL (unreadable file or bad row; the table is
@@ -140,6 +149,21 @@ const char* tdp_last_error(void);
 /* Number of kernels this library has launched in this process (all
  * streams); lets callers count launches inside a timed region. */
 int64_t tdp_launch_count(void);
+
+/* Launch tuning knobs, process-wide (change them between solves, not while
+ * another thread is solving).  Start values come from environment variables
+ * of the same names.  tdp_set_tuning returns TDP_OK or TDP_EINVAL (unknown
+ * key or value out of range); tdp_get_tuning returns the value or -1. */
+#define TDP_TUNE_SMEM_BUDGET 0  /* shared memory per CTA of the register-staged tiles, bytes [4096, 232448] */
+#define TDP_TUNE_S_REC 1        /* sub-system size inside the interface recursion [3, 1024] */
+#define TDP_TUNE_S_TAIL 2       /* sub-system size in the one-launch tail of that recursion [3, 256] */
+#define TDP_TUNE_VTILE 3        /* 1: 16-byte cp.async interleaved tiles for single systems */
+#define TDP_TUNE_COOP 4         /* 1: the small interface levels in one cooperative launch */
+#define TDP_TUNE_FUSED_REFINE 5 /* 1: one fused pass per refinement correction */
+#define TDP_TUNE_TMA 6          /* 1: TMA-staged tiles */
+#define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline */
+int tdp_set_tuning(int key, int value);
+int tdp_get_tuning(int key);
 
 /* Per-kernel timing (a tracing aid): when enabled, every kernel the library
  * launches outside stream capture is bracketed by two CUDA events recorded

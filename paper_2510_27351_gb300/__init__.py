@@ -58,6 +58,9 @@ def _load() -> ctypes.CDLL:
     lib.tdp_profile_summary.argtypes = [ctypes.c_char_p, I64]
     lib.tdp_profile_summary.restype = I64
     lib.tdp_solve_noalloc.argtypes = [P, P, P, P, P, I64, I32, I32, P]
+    lib.tdp_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.tdp_predict_s_batched.argtypes = [P, I32, I32, P, P]
+    lib.tdp_get_tuning.argtypes = [ctypes.c_int]
     return lib
 
 
@@ -67,7 +70,9 @@ LIB = _load()
 SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_backward", "tdp_predict_s",
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
-           "tdp_solve_noalloc")
+           "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched")
+
+TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE = range(8)
 
 
 def _check(rc: int):
@@ -148,6 +153,10 @@ def tdp_predict_s(n: int, batch: int = 1, dtype: int = F64) -> int:
     return int(LIB.tdp_predict_s(int(n), int(batch), int(dtype)))
 
 
+def tdp_predict_s_batched(offsets, batch, dtype, s_out, stream=None):
+    _check(LIB.tdp_predict_s_batched(_ptr(offsets), int(batch), int(dtype), _ptr(s_out), _stream(stream)))
+
+
 def tdp_load_table(path: str):
     _check(LIB.tdp_load_table(path.encode()))
 
@@ -162,6 +171,14 @@ def tdp_status(stream=None):
 
 def tdp_set_checked(on: bool):
     LIB.tdp_set_checked(1 if on else 0)
+
+
+def tdp_set_tuning(key: int, value: int):
+    _check(LIB.tdp_set_tuning(int(key), int(value)))
+
+
+def tdp_get_tuning(key: int) -> int:
+    return int(LIB.tdp_get_tuning(int(key)))
 
 
 def tdp_last_error() -> str:
@@ -228,6 +245,31 @@ def solve_backward(offsets, a, b, c, x, g, s: int = 0, stream=None):
     tdp_solve_backward(offsets, offsets.numel() - 1, x.numel(), a, b, c, x, g, ga, gb, gc, gd, s,
                        _dtype_code(x, False), stream)
     return ga, gb, gc, gd
+
+
+class CapturedSolve:
+    """A solve captured into a CUDA graph.
+
+    ``fn(stream)`` must queue one solve on ``stream`` (for example a
+    ``tdp_solve_batched`` call on fixed buffers).  It runs once un-captured
+    (which sizes the library's workspace for that stream), then once under
+    capture; ``replay()`` re-runs the captured kernels on the same buffers.
+    Checked mode must be off while capturing (it synchronises).
+    """
+
+    def __init__(self, fn, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            fn(self.stream)
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            fn(self.stream)
+        self.stream.synchronize()
+
+    def replay(self):
+        self.graph.replay()
 
 
 class TridiagonalSolve(torch.autograd.Function):

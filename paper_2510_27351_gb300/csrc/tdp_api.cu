@@ -9,6 +9,7 @@
 #include <fstream>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -64,19 +65,47 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
   return &g_ws[{dev, st}];
 }
 
-// Launch knobs for experiments: TDP_PIPELINE=1 selects the warp-tile cp.async
-// pipeline (and the fused refinement pass), TDP_S_REC the sub-system size inside the interface recursion,
-// TDP_SMEM_BUDGET the shared memory per CTA of the non-pipelined kernels.
+// Launch tuning knobs (tdp_set_tuning), process-wide.  Their start values
+// come from the environment: TDP_SMEM_BUDGET (shared memory per CTA aimed
+// for by the register-staged tiles), TDP_S_REC (sub-system size inside the
+// interface recursion), TDP_S_TAIL (inside its one-launch tail), TDP_VTILE,
+// TDP_COOP, TDP_FUSED_REFINE, TDP_TMA, TDP_PIPELINE (0/1 switches of the
+// interleaved tiles, the one-launch tail, the fused refinement passes, the
+// TMA-staged tiles and the warp-tile pipeline).
+struct Knob {
+  const char* env;
+  int lo, hi;
+  std::atomic<int> v;
+};
+Knob g_knobs[8] = {
+    {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {32}},
+    {"TDP_S_TAIL", 3, 256, {16}},                          {"TDP_VTILE", 0, 1, {1}},
+    {"TDP_COOP", 0, 1, {0}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
+    {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
+};
+std::once_flag g_knobs_once;
+
+void knobs_init() {
+  std::call_once(g_knobs_once, [] {
+    for (Knob& k : g_knobs) {
+      if (const char* v = std::getenv(k.env)) {
+        const int r = std::atoi(v);
+        if (r >= k.lo && r <= k.hi) k.v.store(r);
+      }
+    }
+  });
+}
+
 void tune_from_env(Ctx& ctx) {
-  if (const char* v = std::getenv("TDP_PIPELINE")) ctx.pipeline = std::atoi(v) != 0;
-  if (const char* v = std::getenv("TDP_S_REC")) {
-    const int r = std::atoi(v);
-    if (r >= 3 && r <= 1024) ctx.s_rec = r;
-  }
-  if (const char* v = std::getenv("TDP_SMEM_BUDGET")) {
-    const int r = std::atoi(v);
-    if (r >= 4096 && r <= 227 * 1024) ctx.smem_budget = r;
-  }
+  knobs_init();
+  ctx.smem_budget = g_knobs[TDP_TUNE_SMEM_BUDGET].v.load();
+  ctx.s_rec = g_knobs[TDP_TUNE_S_REC].v.load();
+  ctx.s_tail = g_knobs[TDP_TUNE_S_TAIL].v.load();
+  ctx.vtile = g_knobs[TDP_TUNE_VTILE].v.load() != 0;
+  ctx.coop = g_knobs[TDP_TUNE_COOP].v.load() != 0;
+  ctx.fused_refine = g_knobs[TDP_TUNE_FUSED_REFINE].v.load() != 0;
+  ctx.tma = g_knobs[TDP_TUNE_TMA].v.load() != 0;
+  ctx.pipeline = g_knobs[TDP_TUNE_PIPELINE].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.
@@ -346,9 +375,8 @@ int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, co
   if (!offsets) return set_error(TDP_EINVAL, "tdp_solve_batched: null offsets");
   if (total_n == 0) return TDP_OK;
   if ((rc = check_ptrs({a, b, c, d, x}, "tdp_solve_batched"))) return rc;
-  const int ss = s ? s : predict_s((total_n + batch - 1) / batch, batch, dtype);
   return run(stream, "tdp_solve_batched", [&](Ctx& ctx) {
-    solve_batched(ctx, offsets, batch, total_n, a, b, c, d, x, ss, dtype, refine_iters);
+    solve_batched(ctx, offsets, batch, total_n, a, b, c, d, x, s, dtype, refine_iters);
   });
 }
 
@@ -381,6 +409,14 @@ int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, c
   return run(stream, "tdp_solve_backward", [&](Ctx& ctx) {
     solve_backward(ctx, offsets, batch, total_n, a, b, c, x, g, grad_a, grad_b, grad_c, grad_d, ss, dtype);
   });
+}
+
+int tdp_predict_s_batched(const int64_t* offsets, int32_t batch, tdp_dtype dtype, int32_t* s_out, void* stream) {
+  if (batch < 1) return set_error(TDP_EINVAL, "tdp_predict_s_batched: batch must be >= 1");
+  if (!offsets || !s_out) return set_error(TDP_EINVAL, "tdp_predict_s_batched: null pointer");
+  if (dtype != TDP_F64 && dtype != TDP_F32 && dtype != TDP_F32_REFINE)
+    return set_error(TDP_EINVAL, "tdp_predict_s_batched: unsupported dtype");
+  return run(stream, "tdp_predict_s_batched", [&](Ctx& ctx) { predict_sizes(ctx, offsets, batch, dtype, s_out); });
 }
 
 int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype) {
@@ -426,6 +462,24 @@ int tdp_status(void* stream) {
 }
 
 void tdp_set_checked(int on) { g_checked.store(on ? 1 : 0); }
+
+int tdp_set_tuning(int key, int value) {
+  knobs_init();
+  if (key < 0 || key >= int(sizeof(g_knobs) / sizeof(g_knobs[0])))
+    return set_error(TDP_EINVAL, "tdp_set_tuning: unknown key");
+  Knob& k = g_knobs[key];
+  if (value < k.lo || value > k.hi)
+    return set_error(TDP_EINVAL, std::string("tdp_set_tuning: ") + k.env + " must be in [" + std::to_string(k.lo) +
+                                     ", " + std::to_string(k.hi) + "]");
+  k.v.store(value);
+  return TDP_OK;
+}
+
+int tdp_get_tuning(int key) {
+  knobs_init();
+  if (key < 0 || key >= int(sizeof(g_knobs) / sizeof(g_knobs[0]))) return -1;
+  return g_knobs[key].v.load();
+}
 
 const char* tdp_last_error(void) { return g_last_error.c_str(); }
 

@@ -37,6 +37,11 @@ struct Ctx {
   int s_rec = 32;              // sub-system size inside the interface-system recursion
   bool pipeline = false;       // warp-tile cp.async pipeline (TDP_PIPELINE=1); slower on GB300 so far
   bool events_ok = true;       // the profiler may create CUDA events around launches
+  bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
+  bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
+  bool coop = false;           // small interface levels in one cooperative launch (TDP_COOP=1)
+  int s_tail = 16;             // sub-system size inside that launch (TDP_S_TAIL)
+  bool fused_refine = false;   // one fused pass per refinement correction (TDP_FUSED_REFINE=1)
   std::string msg;
   void fail(cudaError_t e, const char* where) {
     if (err == cudaSuccess && e != cudaSuccess) {
@@ -56,6 +61,7 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
                   int s, tdp_dtype dt, int refine_iters);
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
                    const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
+void predict_sizes(Ctx& ctx, const int64_t* offsets, int32_t batch, tdp_dtype dt, int32_t* s_out);
 void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
                    const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
 void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,

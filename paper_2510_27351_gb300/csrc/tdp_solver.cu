@@ -2,14 +2,19 @@
 // stages of the partition method (Sec. I), for single, batched, strided and
 // transposed (adjoint) solves.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <map>
 #include <mutex>
 #include <set>
+#include <tuple>
+#include <type_traits>
 #include <utility>
 
 #include "tdp_internal.h"
-#include "tdp_pipe.cuh"
+#include "tdp_tma.cuh"
+#include "tdp_vtile.cuh"
+#include "tdp_coop.cuh"
 
 namespace tdp {
 
@@ -116,6 +121,72 @@ size_t warp_bytes(int s, int ld, int el, bool mapped, int arrays) {
   return 2 * (b + o);
 }
 
+// Leading dimension of a CTA tile of T blocks for the transpose pass (thread
+// i moves rows i, i + T, ...): the smallest ld >= T with the fewest
+// shared-memory wavefronts per warp, simulated bank by bank.
+int pick_ld_cta(int s, int el, int T) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> memo;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = memo.find({s, el, T});
+  if (it != memo.end()) return it->second;
+  int best = 1 << 30, best_ld = T + 1;
+  const int group = (el == 8) ? 16 : 32;
+  for (int ld = T; ld < T + 64; ++ld) {
+    int worst = 0;
+    for (int base = 0; base < std::min(T * s, 32 * 64); base += 32) {
+      int cost = 0;
+      for (int g0 = 0; g0 < 32; g0 += group) {
+        int hits[32] = {0};
+        int mx = 0;
+        for (int l = g0; l < g0 + group; ++l) {
+          const int p = base + l;
+          const int t = p / s, j = p % s;
+          mx = std::max(mx, ++hits[(j * ld + t) % group]);
+        }
+        cost += mx;
+      }
+      worst = std::max(worst, cost);
+    }
+    if (worst < best) {
+      best = worst;
+      best_ld = ld;
+    }
+  }
+  memo[{s, el, T}] = best_ld;
+  return best_ld;
+}
+
+struct TmaCfg {
+  bool ok = false;
+  int T = 0, ld = 0, grid = 1;
+  size_t smem = 0;
+};
+
+template <typename S, bool MAPPED, int NA, typename K>
+TmaCfg tma_cfg(K kern, int s, int64_t m) {
+  TmaCfg c;
+  for (int T = 256; T >= 32; T /= 2) {
+    const int ld = pick_ld_cta(s, sizeof(S), T);
+    const size_t bytes = TmaBufs<S, MAPPED, NA>::bytes(T, s, ld);
+    if (bytes <= size_t(kMaxSmem)) {
+      c.T = T;
+      c.ld = ld;
+      c.smem = bytes;
+      break;
+    }
+  }
+  if (!c.T) return c;
+  allow_smem(kern);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.T, c.smem) != cudaSuccess || per_sm < 1)
+    return c;
+  const int64_t tiles = (m + c.T - 1) / c.T;
+  c.grid = int(std::max<int64_t>(1, std::min<int64_t>(tiles, int64_t(per_sm) * sm_count())));
+  c.ok = true;
+  return c;
+}
+
 constexpr size_t kPipeWarpMax = 113 * 1024;  // at least two warps per SM
 
 // Warps per CTA of the pipelined kernels (each warp has its own buffers, so
@@ -164,6 +235,28 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
             const char* name = nullptr) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
   const char* nm = name ? name : KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32");
+  if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
+    size_t smem;
+    const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
+    auto vk = k_stage1_v<S, C, KEEP>;
+    allow_smem(vk);
+    pre_launch(ctx, nm);
+    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
+                                                           ctx.status);
+    post_launch(ctx, "stage 1");
+    return;
+  }
+  if (ctx.tma) {
+    auto tk = k_stage1_tma<S, C, MAPPED, KEEP>;
+    const TmaCfg tc = tma_cfg<S, MAPPED, 4>(tk, s, m);
+    if (tc.ok) {
+      pre_launch(ctx, nm);
+      tk<<<tc.grid, tc.T, tc.smem, ctx.stream>>>(a, b, c, d, n, s, tc.ld, magic_for(s), m, blk, ra, rb, rc, rd, ka,
+                                                  kg, kd, ctx.status);
+      post_launch(ctx, "stage 1");
+      return;
+    }
+  }
   if (ctx.pipeline) {
     auto pk = k_stage1_pipe<S, C, MAPPED, KEEP>;
     const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
@@ -205,6 +298,26 @@ template <typename S, typename C, bool MAPPED>
 void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
                     const int64_t* blk, const double* y, S* x) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
+    size_t smem;
+    const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
+    auto vk = k_stage3_resolve_v<S, C>;
+    allow_smem(vk);
+    pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
+    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.status);
+    post_launch(ctx, "stage 3");
+    return;
+  }
+  if (ctx.tma) {
+    auto tk = k_stage3_resolve_tma<S, C, MAPPED>;
+    const TmaCfg tc = tma_cfg<S, MAPPED, 4>(tk, s, m);
+    if (tc.ok) {
+      pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
+      tk<<<tc.grid, tc.T, tc.smem, ctx.stream>>>(a, b, c, d, n, s, tc.ld, magic_for(s), m, blk, y, x, ctx.status);
+      post_launch(ctx, "stage 3");
+      return;
+    }
+  }
   if (ctx.pipeline) {
     auto pk = k_stage3_resolve_pipe<S, C, MAPPED>;
     const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
@@ -231,9 +344,70 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
 // partition method to it again (the recursive variant, Sec. III) until it is
 // small enough for one thread.
 // ---------------------------------------------------------------------------
+constexpr int64_t kCoopMax = int64_t(1) << 19;  // interface systems at most this large go to one launch
+
+// All remaining recursion levels of an interface system of M rows in one
+// cooperative launch (k_iface_coop).
+void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
+                          double* y, int64_t M) {
+  CoopParams P{};
+  int L = 0;
+  const double *a = ra, *b = rb, *c = rc, *d = rd;
+  double* yl = y;
+  int64_t Ml = M;
+  while (Ml > kBaseRows && L < kCoopMaxLevels) {
+    CoopLevel& D = P.lv[L];
+    D.s = ctx.s_tail;
+    D.M = Ml;
+    D.m = (Ml + D.s - 1) / D.s;
+    D.a = a; D.b = b; D.c = c; D.d = d;
+    D.ka = ctx.ar->take<double>(Ml);
+    D.kg = ctx.ar->take<double>(Ml);
+    D.kd = ctx.ar->take<double>(Ml);
+    D.na = ctx.ar->take<double>(2 * D.m);
+    D.nb = ctx.ar->take<double>(2 * D.m);
+    D.nc = ctx.ar->take<double>(2 * D.m);
+    D.nd = ctx.ar->take<double>(2 * D.m);
+    D.y = yl;
+    a = D.na; b = D.nb; c = D.nc; d = D.nd;
+    Ml = 2 * D.m;
+    ++L;
+    if (Ml > kBaseRows && L < kCoopMaxLevels) yl = ctx.ar->take<double>(Ml);
+  }
+  P.L = L;
+  P.base_scratch = ctx.ar->take<double>(Ml);
+  P.ybase = (L > 0) ? ctx.ar->take<double>(Ml) : y;
+  unsigned* bar = ctx.ar->take<unsigned>(2);
+  if (ctx.dry || ctx.err != cudaSuccess) return;
+  ctx.fail(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), ctx.stream), "barrier clear");
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iface_coop, 128, 0) != cudaSuccess) per_sm = 0;
+  }
+  const int64_t want = std::max<int64_t>(1, (P.lv[0].m + 127) / 128);
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(per_sm, 1)) * sm_count())));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  pre_launch(ctx, "iface_coop");
+  ctx.fail(cudaLaunchKernelEx(&cfg, k_iface_coop, P, bar, ctx.status), "interface cooperative launch");
+  post_launch(ctx, "interface cooperative launch");
+}
+
 void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
                      int64_t M) {
   if (M <= 0) return;
+  if (ctx.coop && M > kBaseRows && M <= kCoopMax) {
+    solve_interface_coop(ctx, ra, rb, rc, rd, y, M);
+    return;
+  }
   if (M <= kBaseRows) {
     double* scratch = ctx.ar->take<double>(M);
     if (ctx.dry || ctx.err != cudaSuccess) return;
@@ -268,8 +442,8 @@ void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double*
 // decreasing, or offsets[batch] != total_n) make every count zero and raise
 // ST_BADARG, so that no later kernel touches a row.
 __global__ void __launch_bounds__(1024) k_block_scan(const int64_t* __restrict__ off, int32_t batch, int s,
-                                                     int64_t total_n, int64_t* __restrict__ bbase,
-                                                     unsigned* __restrict__ status) {
+                                                     const int32_t* __restrict__ sj, int64_t total_n,
+                                                     int64_t* __restrict__ bbase, unsigned* __restrict__ status) {
   __shared__ int64_t warp_sums[32];
   __shared__ int bad;
   __shared__ int64_t carry;
@@ -290,7 +464,8 @@ __global__ void __launch_bounds__(1024) k_block_scan(const int64_t* __restrict__
   for (int64_t j0 = 0; j0 < batch; j0 += blockDim.x) {
     const int64_t j = j0 + tid;
     const int64_t len = (j < batch) ? off[j + 1] - off[j] : 0;
-    int64_t v = (len + s - 1) / s;
+    const int sz = (sj && j < batch) ? sj[j] : s;
+    int64_t v = (len + sz - 1) / sz;
     // inclusive warp scan
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
@@ -308,7 +483,7 @@ __global__ void __launch_bounds__(1024) k_block_scan(const int64_t* __restrict__
     }
     __syncthreads();
     const int64_t incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
-    const int64_t excl = incl - ((j < batch) ? (off[j + 1] - off[j] + s - 1) / s : 0);
+    const int64_t excl = incl - ((j < batch) ? (off[j + 1] - off[j] + sz - 1) / sz : 0);
     if (j < batch) bbase[j] = excl;
     __syncthreads();
     if (tid == int(blockDim.x) - 1) carry = incl;
@@ -317,10 +492,47 @@ __global__ void __launch_bounds__(1024) k_block_scan(const int64_t* __restrict__
   if (tid == 0) bbase[batch] = carry;
 }
 
+// ---------------------------------------------------------------------------
+// Size model inference on the device (Sec. II-E): for every system j, the
+// label of the nearest table row in (log2 N_j, log2 batch), ties to the
+// larger s.  The table travels as a kernel parameter.
+// ---------------------------------------------------------------------------
+constexpr int kKpMax = 256;
+struct KpTable {
+  int rows;
+  double f[2 * kKpMax];
+  int32_t lab[kKpMax];
+};
+
+__global__ void k_predict_sizes(const int64_t* __restrict__ off, int32_t batch, const __grid_constant__ KpTable tab,
+                                int fallback, int clamp, int32_t* __restrict__ s_out) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  int64_t n = off[j + 1] - off[j];
+  if (n < 1) n = 1;
+  const double ln = log2(double(n)), lb = log2(double(batch));
+  double best = 1e300;
+  int s = 0;
+  for (int r = 0; r < tab.rows; ++r) {
+    const double dn = tab.f[2 * r] - ln, db = tab.f[2 * r + 1] - lb;
+    const double dist = dn * dn + db * db;
+    if (dist < best || (dist == best && tab.lab[r] > s)) {
+      best = dist;
+      s = tab.lab[r];
+    }
+  }
+  if (tab.rows == 0) {  // no table: the paper's interval rule (Sec. II-D)
+    s = n <= 4500 ? 4 : n <= 25000 ? 8 : n <= 50000 ? 16 : n <= 75000 ? 20 : n <= 10000000 ? 32 : 64;
+  }
+  s = s >= 2 ? s : fallback;
+  s_out[j] = s < clamp ? s : clamp;  // the tiles are sized for clamp rows per block
+}
+
 // blk[k] for k < m_max: start row of block k with flags; dummy blocks (after
 // the last real one) start at total_n and are empty.  blk[m_max] = total_n.
-__global__ void k_block_fill(const int64_t* __restrict__ off, int32_t batch, int s, int64_t total_n,
-                             const int64_t* __restrict__ bbase, int64_t m_max, int64_t* __restrict__ blk) {
+__global__ void k_block_fill(const int64_t* __restrict__ off, int32_t batch, int s, const int32_t* __restrict__ sj,
+                             int64_t total_n, const int64_t* __restrict__ bbase, int64_t m_max,
+                             int64_t* __restrict__ blk) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k > m_max) return;
   if (k == m_max || k >= bbase[batch]) {
@@ -335,7 +547,7 @@ __global__ void k_block_fill(const int64_t* __restrict__ off, int32_t batch, int
   }
   const int64_t i = k - bbase[lo];
   const int64_t cnt = bbase[lo + 1] - bbase[lo];
-  int64_t e = off[lo] + i * s;
+  int64_t e = off[lo] + i * (sj ? sj[lo] : s);
   if (i == 0) e |= BLK_FIRST;
   if (i == cnt - 1) e |= BLK_LAST;
   blk[k] = e;
@@ -428,6 +640,43 @@ unsigned grid_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------------------
+// Refinement with the fused CTA-tile pass (k_refine_pass_cta).  Same
+// schedule as refine_fused; HBM traffic 4 + 5 + 6q words per row for q
+// corrections.
+// ---------------------------------------------------------------------------
+template <bool MAPPED>
+bool refine_fused_cta(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                      int s, int64_t m, const int64_t* blk, double* ra, double* rb, double* rc, double* rd, double* y,
+                      int iters) {
+  auto bytes = [&](int T) { return size_t(6) * 8 * s * (T + 1) + (MAPPED ? size_t(4) * T * s : 0); };
+  int T = 256;
+  while (T > 32 && bytes(T) > size_t(ctx.smem_budget)) T /= 2;
+  while (T > 1 && bytes(T) > size_t(kMaxSmem)) --T;
+  if (bytes(T) > size_t(kMaxSmem)) return false;
+  const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
+  double* rd2 = ctx.ar->take<double>(iters > 0 ? 2 * m : 1);
+  double* xb[2] = {ctx.ar->take<double>(iters > 0 ? n : 1), ctx.ar->take<double>(iters > 1 ? n : 1)};
+  stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                       (float*)nullptr, (float*)nullptr);
+  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+  for (int it = 0; it <= iters; ++it) {
+    const double* xin = it == 0 ? nullptr : xb[(it - 1) & 1];
+    double* xo = it == iters ? (double*)x : xb[it & 1];
+    double* rdn = it < iters ? rd2 : nullptr;
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      auto kern = it == 0 ? k_refine_pass_cta<MAPPED, false> : k_refine_pass_cta<MAPPED, true>;
+      allow_smem(kern);
+      pre_launch(ctx, "refine_pass");
+      kern<<<unsigned((m + T - 1) / T), T, bytes(T), ctx.stream>>>(A, B, Cc, D, xin, n, s, magic_for(s), m, blk, y,
+                                                                   xo, rdn, ctx.status);
+      post_launch(ctx, "refine pass");
+    }
+    if (it < iters) solve_interface(ctx, ra, rb, rc, rd2, y, 2 * m);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Refinement with the fused pass (k_refine_pass): Stage 1 in binary32, then
 // per correction one pass that finishes the previous correction, updates x
 // in binary64 and prepares the next interface right-hand side.  HBM traffic
@@ -438,7 +687,8 @@ template <bool MAPPED>
 bool refine_fused(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
                   int64_t m, const int64_t* blk, double* ra, double* rb, double* rc, double* rd, double* y,
                   int iters) {
-  if (!ctx.pipeline) return false;
+  if (!ctx.fused_refine) return false;
+  if (!ctx.pipeline) return refine_fused_cta<MAPPED>(ctx, a, b, c, d, x, n, s, m, blk, ra, rb, rc, rd, y, iters);
   const size_t per = warp_bytes(s, pick_ld(s, 8), 8, MAPPED, 6);
   if (per > kPipeWarpMax) return false;
   const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
@@ -532,21 +782,60 @@ struct BatchMap {
   int64_t m = 0;
 };
 
-BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, int s, bool need_edges) {
+// Per-system sizes: the device predictor writes s_j for every system (the
+// table rows of dtype dt); returns false when that table is empty.
+struct SizeModel {
+  KpTable tab;
+  int s_min = 0, s_max = 0;
+};
+
+bool size_model(tdp_dtype dt, int32_t batch, SizeModel* sm) {
+  const float* feat = nullptr;
+  const int32_t* lab = nullptr;
+  const int rows = std::min(predictor_table(dt, &feat, &lab), kKpMax);
+  if (rows <= 0) return false;
+  sm->tab.rows = rows;
+  sm->s_min = 1 << 30;
+  sm->s_max = 0;
+  // tiles are sized for the largest label among the rows of the nearest batch size
+  const double lb = std::log2(double(std::max(1, batch)));
+  double near = 1e300;
+  for (int r = 0; r < rows; ++r) near = std::min(near, std::fabs(double(feat[2 * r + 1]) - lb));
+  for (int r = 0; r < rows; ++r) {
+    sm->tab.f[2 * r] = feat[2 * r];
+    sm->tab.f[2 * r + 1] = feat[2 * r + 1];
+    sm->tab.lab[r] = lab[r];
+    sm->s_min = std::min(sm->s_min, int(lab[r]));
+    if (std::fabs(double(feat[2 * r + 1]) - lb) <= near) sm->s_max = std::max(sm->s_max, int(lab[r]));
+  }
+  sm->s_min = std::min(sm->s_min, sm->s_max);
+  return true;
+}
+
+BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, int s, bool need_edges,
+                   const SizeModel* model = nullptr) {
   BatchMap bm;
-  bm.m = (total_n + int64_t(batch) * (s - 1)) / s;
+  const int s_lo = model ? model->s_min : s;
+  bm.m = (total_n + int64_t(batch) * (s_lo - 1)) / s_lo;
   int64_t* bbase = ctx.ar->take<int64_t>(batch + 1);
   int64_t* blk = ctx.ar->take<int64_t>(bm.m + 1);
   uint8_t* edge = need_edges ? ctx.ar->take<uint8_t>(total_n) : nullptr;
+  int32_t* sj = model ? ctx.ar->take<int32_t>(batch) : nullptr;
   bm.blk = blk;
   bm.edge = edge;
   if (ctx.dry || ctx.err != cudaSuccess) return bm;
+  if (model) {
+    pre_launch(ctx, "predict_sizes");
+    k_predict_sizes<<<unsigned((batch + 127) / 128), 128, 0, ctx.stream>>>(offsets, batch, model->tab,
+                                                                           model->s_max, model->s_max, sj);
+    post_launch(ctx, "predict sizes");
+  }
   pre_launch(ctx, "block_scan");
-  k_block_scan<<<1, 1024, 0, ctx.stream>>>(offsets, batch, s, total_n, bbase, ctx.status);
+  k_block_scan<<<1, 1024, 0, ctx.stream>>>(offsets, batch, s, sj, total_n, bbase, ctx.status);
   post_launch(ctx, "block scan");
   pre_launch(ctx, "block_fill");
-  k_block_fill<<<unsigned((bm.m + 1 + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, s, total_n, bbase, bm.m,
-                                                                         blk);
+  k_block_fill<<<unsigned((bm.m + 1 + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, s, sj, total_n, bbase,
+                                                                         bm.m, blk);
   post_launch(ctx, "block fill");
   if (need_edges && total_n > 0) {
     ctx.fail(cudaMemsetAsync(edge, 0, size_t(total_n), ctx.stream), "edge clear");
@@ -572,8 +861,32 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                    const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
   if (batch <= 0 || total_n <= 0) return;
-  BatchMap bm = build_map(ctx, offsets, batch, total_n, s, dt == TDP_F32_REFINE && refine_iters > 0);
+  const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;
+  if (s == 0) {
+    // per-system sizes from the device predictor; tiles sized for the largest
+    static thread_local SizeModel model;
+    if (size_model(dt, batch, &model)) {
+      BatchMap bm = build_map(ctx, offsets, batch, total_n, model.s_max, edges, &model);
+      solve_blocks<true>(ctx, a, b, c, d, x, total_n, model.s_max, bm.m, bm.blk, bm.edge, dt, refine_iters);
+      return;
+    }
+    s = predict_s((total_n + batch - 1) / batch, batch, dt);
+  }
+  BatchMap bm = build_map(ctx, offsets, batch, total_n, s, edges);
   solve_blocks<true>(ctx, a, b, c, d, x, total_n, s, bm.m, bm.blk, bm.edge, dt, refine_iters);
+}
+
+void predict_sizes(Ctx& ctx, const int64_t* offsets, int32_t batch, tdp_dtype dt, int32_t* s_out) {
+  static thread_local SizeModel model;
+  if (ctx.dry || ctx.err != cudaSuccess) return;
+  if (!size_model(dt, batch, &model)) {
+    model.tab.rows = 0;
+    model.s_max = predict_s(1, batch, dt);
+  }
+  pre_launch(ctx, "predict_sizes");
+  k_predict_sizes<<<unsigned((batch + 127) / 128), 128, 0, ctx.stream>>>(offsets, batch, model.tab, model.s_max,
+                                                                         1024, s_out);
+  post_launch(ctx, "predict sizes");
 }
 
 void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, const void* a, const void* b,

@@ -1,0 +1,336 @@
+"""Sub-system-size model: timing sweeps on the GPU, label correction, 1-NN.
+
+This is the GB300 counterpart of the paper's heuristic (Sec. II-D, II-E,
+IV-B): time the solver for every sub-system size s of a grid at many sizes
+N, take the fastest s per N, correct the labels towards a trend, and fit a
+1-nearest-neighbour classifier N -> s (one per precision; the batch size is
+a second feature for batched solves).  The library's predictor
+(``tdp_predict_s``, host and device) reads the resulting table.
+
+    python -m paper_2510_27351_gb300.tune sweep --out sweep.jsonl
+    python -m paper_2510_27351_gb300.tune table --sweep sweep.jsonl --out table.txt --inc csrc/tdp_table.inc
+    python -m paper_2510_27351_gb300.tune evaluate --sweep sweep.jsonl
+
+The sweep appends one JSON line per (dtype, n, batch, s) so that a killed
+sweep resumes where it stopped.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import random
+import sys
+from collections import defaultdict
+
+S_GRID = (4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 96, 128)
+DTYPES = {0: "f64", 1: "f32", 2: "f32_refine"}
+TOL = 0.05  # labels within 5 % of the fastest count as near-optimal
+
+
+# ---------------------------------------------------------------------------
+# label correction (Sec. II-E)
+# ---------------------------------------------------------------------------
+def correct(times, tol: float = TOL):
+    """``times``: per ascending size, a dict {s: time}.  Returns (raw, corrected).
+
+    Raw label: the fastest s (ties to the larger s).  Corrected: among the
+    sizes within ``tol`` of the fastest, a non-decreasing sequence over N with
+    the fewest label changes, preferring larger labels (compared from the
+    largest N down), then the least total relative loss.
+    """
+    n = len(times)
+    raw = []
+    cand = []
+    for t in times:
+        best = min(t.values())
+        raw.append(max((s for s in t if t[s] == best)))
+        cand.append({s: t[s] / best - 1.0 for s in t if t[s] <= (1.0 + tol) * best})
+    # state per position: label -> (changes, labels from the end (negated), loss, path)
+    table = [None] * n
+    table[n - 1] = {s: (0, (-s,), lo, [s]) for s, lo in cand[n - 1].items()}
+    for i in range(n - 2, -1, -1):
+        cur = {}
+        for s, lo in cand[i].items():
+            best = None
+            for s2, (ch, neg, loss, path) in table[i + 1].items():
+                if s2 < s:
+                    continue
+                key = (ch + (1 if s2 != s else 0), neg + (-s,), loss + lo)
+                if best is None or key < best[:3]:
+                    best = key + (path + [s],)
+            if best is not None:
+                cur[s] = best
+        table[i] = cur
+    if not table[0]:
+        raise ValueError("no non-decreasing label sequence within the tolerance")
+    final = min(table[0].values(), key=lambda v: v[:3])
+    return raw, final[3][::-1]
+
+
+# ---------------------------------------------------------------------------
+# 1-nearest neighbour (Sec. II-E) in log2 features
+# ---------------------------------------------------------------------------
+def nearest(train, n, batch=1):
+    """train: list of (n, batch, s).  The label of the closest row in
+    (log2 n, log2 batch); equal distances go to the larger s."""
+    ln, lb = math.log2(max(1, n)), math.log2(max(1, batch))
+    best, lab = None, None
+    for tn, tb, s in train:
+        dist = (math.log2(tn) - ln) ** 2 + (math.log2(tb) - lb) ** 2
+        if best is None or dist < best or (dist == best and s > lab):
+            best, lab = dist, s
+    return lab
+
+
+def load_sweep(path):
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if line:
+                rows.append(json.loads(line))
+    return rows
+
+
+def grouped(rows):
+    """{(dtype, batch): [(n, {s: ms}), ...] ascending n}."""
+    g = defaultdict(lambda: defaultdict(dict))
+    for r in rows:
+        g[(r["dtype"], r["batch"])][r["n"]][r["s"]] = r["ms"]
+    return {k: sorted(v.items()) for k, v in g.items()}
+
+
+def correct_flat(times, tol: float = TOL):
+    """Labels within ``tol`` of the fastest at every N with the fewest label
+    changes over N (no monotonicity), then the least total relative loss."""
+    cand = []
+    for t in times:
+        best = min(t.values())
+        cand.append({s: t[s] / best - 1.0 for s in t if t[s] <= (1.0 + tol) * best})
+    prev = {s: (0, lo, [s]) for s, lo in cand[0].items()}
+    for i in range(1, len(times)):
+        cur = {}
+        for s, lo in cand[i].items():
+            best = None
+            for sp, (ch, loss, path) in prev.items():
+                key = (ch + (1 if sp != s else 0), loss + lo)
+                if best is None or key < best[:2] or (key == best[:2] and sp > best[2][-1]):
+                    best = key + (path + [s],)
+            cur[s] = best
+        prev = cur
+    return min(prev.values(), key=lambda v: (v[0], v[1], -v[2][-1]))[2]
+
+
+def correct_relaxed(times, tol: float = TOL):
+    """The paper's correction (non-decreasing labels, ``correct``) when a
+    sequence within ``tol`` exists; otherwise, since the optimum need not grow
+    with N on every GPU, the flattest labels within ``tol`` (``correct_flat``).
+    Returns (raw, corrected, rule) with rule "monotone" or "flat"."""
+    raw = [max((s for s in tm if tm[s] == min(tm.values()))) for tm in times]
+    try:
+        return correct(times, tol)[0], correct(times, tol)[1], "monotone"
+    except ValueError:
+        return raw, correct_flat(times, tol), "flat"
+
+
+def build_table(rows):
+    """Rows (dtype, n, batch, s) of the corrected labels."""
+    out = []
+    for (dt, batch), series in sorted(grouped(rows).items()):
+        sizes = [n for n, _ in series]
+        raw, cor, _ = correct_relaxed([t for _, t in series])
+        out += [(dt, n, batch, s) for n, s in zip(sizes, cor)]
+    return out
+
+
+def write_table(table, path_txt=None, path_inc=None):
+    if path_txt:
+        with open(path_txt, "w") as fh:
+            fh.write("# dtype n batch s   (GB300 sweep, corrected labels)\n")
+            for dt, n, b, s in table:
+                fh.write(f"{dt} {n} {b} {s}\n")
+    if path_inc:
+        with open(path_inc, "w") as fh:
+            fh.write("// Built-in predictor table: (dtype, n, batch, s) rows, the corrected labels of\n"
+                     "// the GB300 timing sweep written by paper_2510_27351_gb300/tune.py.  A dtype\n"
+                     "// with no rows falls back to the paper's interval rule.\n"
+                     "static const Row kBuiltinTable[] = {\n")
+            for dt, n, b, s in table:
+                fh.write(f"    {{{dt}, {float(n)!r}, {float(b)!r}, {s}}},\n")
+            fh.write("};\n")
+
+
+def evaluate(rows, seed=0):
+    """The paper's protocol per (dtype, batch): shuffled 3:1 split keeping every
+    class in training, 1-NN accuracy on observed and corrected labels, null
+    accuracy, and the time lost by the prediction against the sweep optimum."""
+    report = {}
+    for (dt, batch), series in sorted(grouped(rows).items()):
+        sizes = [n for n, _ in series]
+        times = [t for _, t in series]
+        raw, cor, tol_used = correct_relaxed(times)
+        idx = list(range(len(sizes)))
+        rng = random.Random(seed)
+        for _ in range(1000):
+            rng.shuffle(idx)
+            k = len(idx) // 4
+            test, train = idx[:k], idx[k:]
+            if set(cor[i] for i in train) == set(cor) and set(raw[i] for i in train) == set(raw):
+                break
+        acc = {}
+        for name, lab in (("observed", raw), ("corrected", cor)):
+            tr = [(sizes[i], batch, lab[i]) for i in train]
+            acc[name] = sum(nearest(tr, sizes[i], batch) == lab[i] for i in test) / max(1, len(test))
+        mode = max(set(cor), key=cor.count)
+        null = sum(cor[i] == mode for i in test) / max(1, len(test))
+        tr = [(sizes[i], batch, cor[i]) for i in train]
+        losses = []
+        for i in test:
+            sp = nearest(tr, sizes[i], batch)
+            t = times[i]
+            losses.append(t.get(sp, float("inf")) / min(t.values()) - 1.0)
+        report[f"{DTYPES.get(dt, dt)}/batch{batch}"] = {
+            "n_sizes": len(sizes), "accuracy_observed": acc["observed"], "accuracy_corrected": acc["corrected"],
+            "null_accuracy": null, "max_time_loss": max(losses) if losses else 0.0,
+            "mean_time_loss": sum(losses) / max(1, len(losses)), "correction_rule": tol_used,
+            "test_sizes": [sizes[i] for i in sorted(test)]}
+    return report
+
+
+# ---------------------------------------------------------------------------
+# autotuner for a given batch (GPU)
+# ---------------------------------------------------------------------------
+_AUTOTUNE_CACHE = {}
+
+
+def autotune_batched(offsets, a, b, c, d, x, dtype, refine_iters=0, s_grid=(8, 12, 16, 24, 32, 48),
+                     budgets=(32 * 1024, 64 * 1024, 100 * 1024), reps=3):
+    """Pick (s, shared-memory budget per CTA) for ``tdp_solve_batched`` on
+    this batch by timing every pair, set the budget knob and return
+    (s, budget, ms).  Results are cached per (dtype, total rows, batch)."""
+    import torch
+
+    import paper_2510_27351_gb300 as tdp
+
+    batch, total = offsets.numel() - 1, d.numel()
+    key = (int(dtype), int(total), int(batch), int(refine_iters))
+    if key in _AUTOTUNE_CACHE:
+        s, budget, ms = _AUTOTUNE_CACHE[key]
+        tdp.tdp_set_tuning(tdp.TUNE_SMEM_BUDGET, budget)
+        return s, budget, ms
+    old = tdp.tdp_get_tuning(tdp.TUNE_SMEM_BUDGET)
+    best = None
+    try:
+        for budget in budgets:
+            tdp.tdp_set_tuning(tdp.TUNE_SMEM_BUDGET, budget)
+            for s in s_grid:
+                fn = lambda: tdp.tdp_solve_batched(offsets, batch, total, a, b, c, d, x, s, dtype, refine_iters)
+                fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                if best is None or ms < best[2]:
+                    best = (s, budget, ms)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_SMEM_BUDGET, old)
+    _AUTOTUNE_CACHE[key] = best
+    tdp.tdp_set_tuning(tdp.TUNE_SMEM_BUDGET, best[1])
+    return best
+
+
+# ---------------------------------------------------------------------------
+# the sweep (GPU)
+# ---------------------------------------------------------------------------
+def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(1,), reps=5, s_grid=S_GRID,
+          max_rows=1 << 28):
+    import torch
+
+    import paper_2510_27351_gb300 as tdp
+
+    done = set()
+    if os.path.exists(out):
+        for r in load_sweep(out):
+            done.add((r["dtype"], r["n"], r["batch"], r["s"]))
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    sizes = []
+    x = log2_lo
+    while x <= log2_hi + 1e-9:
+        sizes.append(int(round(2 ** x)))
+        x += step
+    with open(out, "a") as fh:
+        for batch in batches:
+            for n in sizes:
+                total = n * batch
+                if total > max_rows:
+                    continue
+                for dt in dtypes:
+                    todo = [s for s in s_grid if (dt, n, batch, s) not in done and s <= max(4, n)]
+                    if not todo:
+                        continue
+                    st = torch.float32 if dt == 1 else torch.float64
+                    a = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
+                    b = (torch.rand(total, generator=g, device=dev, dtype=st) * 4 + 4)
+                    c = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
+                    d = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
+                    xo = torch.empty_like(d)
+                    off = torch.arange(batch + 1, device=dev, dtype=torch.int64) * n
+                    it = 1 if dt == 2 else 0
+                    for s in todo:
+                        if batch == 1:
+                            fn = lambda: tdp.tdp_solve(a, b, c, d, xo, total, s, dt, it)
+                        else:
+                            fn = lambda: tdp.tdp_solve_batched(off, batch, total, a, b, c, d, xo, s, dt, it)
+                        fn()
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        r = reps if total >= (1 << 20) else 4 * reps
+                        e0.record()
+                        for _ in range(r):
+                            fn()
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1) / r
+                        fh.write(json.dumps({"dtype": dt, "n": n, "batch": batch, "s": s, "ms": ms}) + "\n")
+                        fh.flush()
+                    del a, b, c, d, xo
+                    torch.cuda.empty_cache()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    p = sub.add_parser("sweep")
+    p.add_argument("--out", required=True)
+    p.add_argument("--dtypes", default="0,1,2")
+    p.add_argument("--lo", type=float, default=10.0)
+    p.add_argument("--hi", type=float, default=28.0)
+    p.add_argument("--step", type=float, default=0.5)
+    p.add_argument("--batches", default="1")
+    p.add_argument("--reps", type=int, default=5)
+    p = sub.add_parser("table")
+    p.add_argument("--sweep", required=True)
+    p.add_argument("--out")
+    p.add_argument("--inc")
+    p = sub.add_parser("evaluate")
+    p.add_argument("--sweep", required=True)
+    args = ap.parse_args(argv)
+    if args.cmd == "sweep":
+        sweep(args.out, tuple(int(v) for v in args.dtypes.split(",")), args.lo, args.hi, args.step,
+              tuple(int(v) for v in args.batches.split(",")), args.reps)
+    elif args.cmd == "table":
+        write_table(build_table(load_sweep(args.sweep)), args.out, args.inc)
+    else:
+        print(json.dumps(evaluate(load_sweep(args.sweep)), indent=1))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -83,3 +83,20 @@ def test_predictor_table_loading(tmp_path):
         assert tdp.tdp_predict_s(1000, 1, 0) == 8  # unchanged by the failed loads
     finally:
         tdp.tdp_load_table("")
+
+
+def test_tuning_knobs_validate_and_round_trip():
+    import paper_2510_27351_gb300 as tdp
+
+    old = tdp.tdp_get_tuning(tdp.TUNE_S_REC)
+    try:
+        tdp.tdp_set_tuning(tdp.TUNE_S_REC, 16)
+        assert tdp.tdp_get_tuning(tdp.TUNE_S_REC) == 16
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_set_tuning(tdp.TUNE_S_REC, 2)  # would not shrink the interface system
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_set_tuning(99, 1)
+        assert tdp.tdp_get_tuning(99) == -1
+        assert tdp.tdp_get_tuning(tdp.TUNE_S_REC) == 16
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_S_REC, old)

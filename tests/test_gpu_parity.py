@@ -243,3 +243,72 @@ def test_autograd_function(tdp):
     ref = oracle.adjoint(S.a, S.b, S.c, xo, w)
     for k, t in zip("abcd", (a, b, c, d)):
         assert oracle.rel_err(host(t.grad), ref[k]) <= 1e-12, k
+
+
+def test_device_size_model_matches_host(tdp, tmp_path):
+    import torch
+
+    Sb = W.batched(300, 16, 1 << 20, seed=9)
+    off = dev(Sb.offsets)
+    out = torch.zeros(Sb.batch, dtype=torch.int32, device="cuda")
+    sizes = np.diff(Sb.offsets)
+    for table in (None, "0 100 1 4\n0 3000 1 8\n0 40000 1 16\n0 1000000 1 32\n0 300 300 6\n0 100000 300 24\n"):
+        if table is not None:
+            p = tmp_path / "t.txt"
+            p.write_text(table)
+            tdp.tdp_load_table(str(p))
+        try:
+            tdp.tdp_predict_s_batched(off, Sb.batch, 0, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            ref = [tdp.tdp_predict_s(int(n), Sb.batch, 0) for n in sizes]
+            assert list(got) == ref
+        finally:
+            tdp.tdp_load_table("")
+
+
+def test_batched_per_system_sizes(tdp, tmp_path):
+    import torch
+
+    p = tmp_path / "t.txt"
+    p.write_text("0 64 4096 4\n0 2000 4096 8\n0 20000 4096 32\n2 64 4096 8\n2 50000 4096 16\n")
+    tdp.tdp_load_table(str(p))
+    try:
+        Sb = W.batched(512, 64, 65536, seed=11)
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        a, b, c, d = (dev(v) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+        off = dev(Sb.offsets)
+        for code in (0, 2):
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, 0, code, 1 if code == 2 else 0)
+            torch.cuda.synchronize()
+            assert oracle.rel_err(host(x), ref) <= 1e-12, code
+    finally:
+        tdp.tdp_load_table("")
+
+
+def test_cuda_graph_capture_and_autotune(tdp):
+    import torch
+
+    from paper_2510_27351_gb300 import tune
+
+    Sb = W.batched(128, 64, 8192, seed=12)
+    a, b, c, d = (dev(v) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+    off = dev(Sb.offsets)
+    x = torch.empty_like(d)
+    tdp.tdp_set_checked(False)
+    try:
+        s, budget, ms = tune.autotune_batched(off, a, b, c, d, x, 2, 1, s_grid=(8, 16), budgets=(32768, 65536))
+        assert s in (8, 16) and budget in (32768, 65536) and ms > 0
+        graph = tdp.CapturedSolve(lambda st: tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, s, 2, 1, st))
+        for seed in (1, 2):  # new right-hand sides in the captured buffers
+            d2 = W.matvec(Sb.a, Sb.b, Sb.c, W.uniform(seed, 9, Sb.n, -1, 1), Sb.offsets)
+            d.copy_(dev(d2))
+            x.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, d2, offsets=Sb.offsets)
+            assert oracle.rel_err(host(x), ref) <= 1e-12
+        tdp.tdp_status()
+    finally:
+        tdp.tdp_set_checked(True)

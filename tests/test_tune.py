@@ -1,0 +1,84 @@
+"""The library's size-model code (tune.py) against the oracle and the paper."""
+import os
+import random
+
+import pytest
+
+from oracle import predictor as P
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table4():
+    rows = P.load_table(os.path.join(GOLD, "table4_fp32_times.txt"))
+    times = []
+    for r in rows:
+        t = {}
+        if r[4] != "-":
+            for kv in r[4:]:
+                s, v = kv.split(":")
+                t[int(s)] = float(v)
+        else:
+            t = {int(r[1]): 1.0}
+        times.append(t)
+    return rows, times
+
+
+def test_correct_reproduces_paper_table4():
+    from paper_2510_27351_gb300 import tune
+
+    rows, times = _table4()
+    raw, cor = tune.correct(times, tol=0.05)
+    assert raw == [int(r[1]) for r in rows]
+    assert cor == [int(r[2]) for r in rows]
+
+
+def test_correct_matches_oracle_on_random_sweeps():
+    from paper_2510_27351_gb300 import tune
+
+    rng = random.Random(3)
+    grid = [4, 8, 16, 20, 32, 64]
+    for _ in range(200):
+        n = rng.randint(2, 12)
+        times = []
+        for i in range(n):
+            best = rng.choice(grid)
+            t = {s: 1.0 + rng.uniform(0, 0.12) + 0.02 * abs(grid.index(s) - grid.index(best)) for s in grid}
+            times.append(t)
+        try:
+            ref = P.correct_labels(times, tol=0.05)
+        except RuntimeError:
+            with pytest.raises(ValueError):
+                tune.correct(times, tol=0.05)
+            continue
+        assert tune.correct(times, tol=0.05) == ref
+
+
+def test_nearest_matches_oracle():
+    from paper_2510_27351_gb300 import tune
+
+    rng = random.Random(5)
+    for _ in range(100):
+        train = [(rng.randint(64, 1 << 26), rng.choice([1, 16, 4096]), rng.choice([4, 8, 16, 32, 64]))
+                 for _ in range(rng.randint(1, 20))]
+        for _ in range(10):
+            n, b = rng.randint(1, 1 << 27), rng.choice([1, 16, 4096, 100])
+            ref = P.knn_predict([t[0] for t in train], [t[2] for t in train], n, 1,
+                                train_batches=[t[1] for t in train], query_batch=b)
+            assert tune.nearest(train, n, b) == ref
+
+
+def test_evaluate_protocol_on_synthetic_sweep():
+    from paper_2510_27351_gb300 import tune
+
+    rows = []
+    for k in range(37):
+        n = int(2 ** (10 + k / 2))
+        opt = 8 if n < 2 ** 14 else 16 if n < 2 ** 20 else 32
+        for s in (8, 16, 32, 64):
+            rows.append({"dtype": 0, "n": n, "batch": 1, "s": s, "ms": 1.0 + 0.1 * abs(s - opt) / opt})
+    rep = tune.evaluate(rows)["f64/batch1"]
+    assert rep["accuracy_corrected"] >= 0.8
+    assert rep["max_time_loss"] <= 0.25
+    table = tune.build_table(rows)
+    assert len(table) == 37 and all(r[3] in (8, 16, 32) for r in table)
