@@ -50,6 +50,27 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def measured_traffic(kernel, s, n):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu capture
+    (profiles/traffic.json), scaled to n rows; None when the kernel sources
+    changed since the capture or the sub-system size differs."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)[kernel]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except (OSError, KeyError, ValueError):
+        return None
+    if h.hexdigest() != rec["sha256"] or int(rec["s"]) != int(s):
+        return None
+    return rec["bytes_per_row"] * n
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -269,7 +290,8 @@ def run_ours(args, world, rank, local):
         flops = STAGE1_F64_FLOPS_PER_ROW * N_MAIN
         ach = flops / (st1[1] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": measured_traffic("stage1_keep_f64", s_main, N_MAIN),
                 "peak_source": "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA/clk x 2 flop",
                 "algorithmic_bytes_per_row": 56 + 64 / s_main,
                 "hbm_frac_of_kernel": (56 + 64 / s_main) * N_MAIN / (st1[1] * 1e-3) / 1e9 / hbm_peak}
@@ -382,8 +404,15 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
         fn = lambda: tdp.tdp_solve_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx, 0,
                                            code, it, stream)
         ms = cuda_time(fn, steps, 2, stream)
-        res[name] = {"ms": ms, "unknowns_per_s": Sb.n / (ms * 1e-3), "hbm_frac_40B": hbm(ms, 40 * Sb.n),
-                     "s": tdp.tdp_predict_s(Sb.n // Sb.batch, Sb.batch, code)}
+        err = float((bx.cpu().numpy() - Sb.xstar).__abs__().max() / np.abs(Sb.xstar).max())
+        # the same solve captured once into a CUDA graph and replayed
+        g = tdp.CapturedSolve(lambda st: tdp.tdp_solve_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"],
+                                                                bdev["c"], bdev["d"], bx, 0, code, it, st))
+        ms_graph = cuda_time(g.replay, steps, 2, g.stream)
+        res[name] = {"ms": ms, "ms_graph": ms_graph, "unknowns_per_s": Sb.n / (ms * 1e-3),
+                     "unknowns_per_s_graph": Sb.n / (ms_graph * 1e-3), "hbm_frac_40B": hbm(ms, 40 * Sb.n),
+                     "s": "per system (device 1-NN)", "rel_err_vs_xstar": err}
+        del g
     fn = lambda: tdp.tdp_thomas_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx,
                                         tdp.F64, stream)
     ms = cuda_time(fn, 2, 1, stream)

@@ -161,7 +161,8 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_COOP 4         /* 1: the small interface levels in one cooperative launch */
 #define TDP_TUNE_FUSED_REFINE 5 /* 1: one fused pass per refinement correction */
 #define TDP_TUNE_TMA 6          /* 1: TMA-staged tiles */
-#define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline */
+#define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline (element copies) */
+#define TDP_TUNE_WTILE 8        /* 1: warp-owned bulk-copy (TMA) tiles for binary32 sweeps of single systems */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

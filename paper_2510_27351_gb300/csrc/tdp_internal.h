@@ -35,7 +35,8 @@ struct Ctx {
   cudaError_t err = cudaSuccess;
   int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
   int s_rec = 32;              // sub-system size inside the interface-system recursion
-  bool pipeline = false;       // warp-tile cp.async pipeline (TDP_PIPELINE=1); slower on GB300 so far
+  bool pipeline = false;       // warp-tile cp.async pipeline with element copies (TDP_PIPELINE=1)
+  bool wtile = false;          // warp-owned bulk-copy tiles (TDP_WTILE=1)
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)

@@ -15,6 +15,7 @@
 #include "tdp_tma.cuh"
 #include "tdp_vtile.cuh"
 #include "tdp_coop.cuh"
+#include "tdp_wtile.cuh"
 
 namespace tdp {
 
@@ -226,6 +227,39 @@ PipeCfg pipe_cfg(K kern, int s, int el, bool mapped, int64_t m, int arrays = 4) 
   return c;
 }
 
+// Warp-owned double-buffered block tiles (tdp_wtile.cuh): warps per CTA and
+// grid.  ok = false when fewer than three warps fit on an SM or the blocks
+// are not 16-byte aligned.
+struct WCfg {
+  bool ok = false;
+  int warps = 1;
+  unsigned grid = 1;
+  size_t smem = 0;
+};
+
+template <typename S, typename K>
+WCfg wtile_cfg(K kern, int s, int64_t m) {
+  WCfg c;
+  constexpr int V = Vec<S>::W;
+  if (s % V != 0) return c;
+  const size_t per = wwarp_bytes<S>(s);
+  if (per * 3 > size_t(kMaxSmem)) return c;
+  c.warps = int(std::min<size_t>(4, size_t(kMaxSmem) / per));
+  c.smem = per * c.warps;
+  allow_smem(kern);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * c.warps, c.smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return c;
+  }
+  const int64_t tiles = (m + 31) / 32;
+  const int64_t want = (tiles + c.warps - 1) / c.warps;
+  c.grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(per_sm) * sm_count())));
+  c.ok = true;
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -235,6 +269,18 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
             const char* name = nullptr) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
   const char* nm = name ? name : KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32");
+  if constexpr (!MAPPED && !KEEP && std::is_same<C, float>::value) {
+    if (ctx.wtile) {
+      auto wk = k_stage1_w<S>;
+      const WCfg wc = wtile_cfg<S>(wk, s, m);
+      if (wc.ok) {
+        pre_launch(ctx, nm);
+        wk<<<wc.grid, 32 * wc.warps, wc.smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ctx.status);
+        post_launch(ctx, "stage 1");
+        return;
+      }
+    }
+  }
   if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
     size_t smem;
     const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
@@ -298,6 +344,18 @@ template <typename S, typename C, bool MAPPED>
 void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
                     const int64_t* blk, const double* y, S* x) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
+  if constexpr (!MAPPED && std::is_same<C, float>::value) {
+    if (ctx.wtile) {
+      auto wk = k_stage3_resolve_w<S>;
+      const WCfg wc = wtile_cfg<S>(wk, s, m);
+      if (wc.ok) {
+        pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
+        wk<<<wc.grid, 32 * wc.warps, wc.smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.status);
+        post_launch(ctx, "stage 3");
+        return;
+      }
+    }
+  }
   if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
     size_t smem;
     const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);

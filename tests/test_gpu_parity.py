@@ -312,3 +312,21 @@ def test_cuda_graph_capture_and_autotune(tdp):
         tdp.tdp_status()
     finally:
         tdp.tdp_set_checked(True)
+
+
+@pytest.mark.parametrize("code", [1, 2])
+def test_warp_bulk_tiles(tdp, code):
+    """The opt-in warp-owned bulk-copy tiles (TDP_TUNE_WTILE) against the oracle:
+    sizes with a ragged last block, an array end inside a 16-byte chunk, and
+    several tiles per warp."""
+    old = tdp.tdp_get_tuning(tdp.TUNE_WTILE)
+    tdp.tdp_set_tuning(tdp.TUNE_WTILE, 1)
+    try:
+        for n in (2, 3, 5, 63, 64, 65, 1000, 4097, 100_003, 1 << 20):
+            S = W.single(n, seed=n + 7)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for s in (2, 4, 8, 12, 24, 32, 64, 100, 128):
+                e = oracle.rel_err(_solve(tdp, S, s, code), ref)
+                assert e <= TOL[code], (n, s, e)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WTILE, old)
