@@ -163,6 +163,7 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_TMA 6          /* 1: TMA-staged tiles */
 #define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline (element copies) */
 #define TDP_TUNE_WTILE 8        /* 1: warp-owned bulk-copy (TMA) tiles for binary32 sweeps of single systems */
+#define TDP_TUNE_REFINE3 9      /* 1: TDP_F32_REFINE runs its solve and first correction as three fused passes */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

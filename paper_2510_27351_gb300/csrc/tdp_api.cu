@@ -69,21 +69,21 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // come from the environment: TDP_SMEM_BUDGET (shared memory per CTA aimed
 // for by the register-staged tiles), TDP_S_REC (sub-system size inside the
 // interface recursion), TDP_S_TAIL (inside its one-launch tail), TDP_VTILE,
-// TDP_COOP, TDP_FUSED_REFINE, TDP_TMA, TDP_PIPELINE, TDP_WTILE (0/1 switches
-// of the interleaved tiles, the one-launch tail, the fused refinement passes,
-// the TMA-staged tiles, the element-copy warp-tile pipeline and the
-// double-buffered 16-byte warp tiles).
+// TDP_COOP, TDP_FUSED_REFINE, TDP_TMA, TDP_PIPELINE, TDP_WTILE, TDP_REFINE3
+// (0/1 switches of the interleaved tiles, the one-launch tail, the fused
+// refinement passes, the TMA-staged tiles, the element-copy warp-tile
+// pipeline, the warp-owned bulk-copy tiles and the three-pass refinement).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[9] = {
+Knob g_knobs[10] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {32}},
     {"TDP_S_TAIL", 3, 256, {16}},                          {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {0}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
     {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
-    {"TDP_WTILE", 0, 1, {0}},
+    {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
 };
 std::once_flag g_knobs_once;
 
@@ -109,6 +109,7 @@ void tune_from_env(Ctx& ctx) {
   ctx.tma = g_knobs[TDP_TUNE_TMA].v.load() != 0;
   ctx.pipeline = g_knobs[TDP_TUNE_PIPELINE].v.load() != 0;
   ctx.wtile = g_knobs[TDP_TUNE_WTILE].v.load() != 0;
+  ctx.refine3 = g_knobs[TDP_TUNE_REFINE3].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

@@ -63,9 +63,26 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double(int(hi | (u & 0x80000000u)), int(lo));
 }
 
+// binary64 -> binary32 with integer operations (the hardware conversion also
+// runs on the binary64 pipe).  The top 32 bits of the 64-bit pattern shifted
+// left by 3 hold the low 9 exponent bits and the top 23 mantissa bits; adding
+// 128 to the exponent field (mod 512) rebiases every exponent of the binary32
+// normal range, and the first dropped mantissa bit rounds to nearest (ties
+// away from zero; a carry into the exponent is the correct next binade).
+// Magnitudes below the binary32 normal range give signed zero, above it
+// infinity; nan stays nan.
+__device__ __forceinline__ float narrow(double v) {
+  const unsigned hi = unsigned(__double2hiint(v)), lo = unsigned(__double2loint(v));
+  const unsigned mag = hi & 0x7fffffffu;
+  unsigned w = (__funnelshift_l(lo, hi, 3) + (128u << 23) + ((lo >> 28) & 1u)) & 0x7fffffffu;
+  if (mag < (897u << 20)) w = 0u;
+  if (mag >= (1151u << 20)) w = (mag > 0x7ff00000u || (mag == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(w | (hi & 0x80000000u));
+}
+
 template <typename C> __device__ __forceinline__ C cvt(double v);
 template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
-template <> __device__ __forceinline__ float cvt<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ float cvt<float>(double v) { return narrow(v); }
 template <typename C> __device__ __forceinline__ C cvt(float v);
 template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
 template <> __device__ __forceinline__ double cvt<double>(float v) { return widen(v); }

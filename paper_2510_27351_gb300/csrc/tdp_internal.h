@@ -37,6 +37,7 @@ struct Ctx {
   int s_rec = 32;              // sub-system size inside the interface-system recursion
   bool pipeline = false;       // warp-tile cp.async pipeline with element copies (TDP_PIPELINE=1)
   bool wtile = false;          // warp-owned bulk-copy tiles (TDP_WTILE=1)
+  bool refine3 = true;         // three fused passes for a solve and its first correction (TDP_REFINE3=0 off)
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)

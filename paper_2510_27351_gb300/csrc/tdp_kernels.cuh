@@ -15,6 +15,8 @@
 // stored (alpha', gamma', delta') or repeats the interior solve with the
 // interface values known.
 #pragma once
+#include <type_traits>
+
 #include "tdp_tile.cuh"
 
 namespace tdp {
@@ -111,6 +113,120 @@ __device__ __forceinline__ IfaceRows block_reduce(S* sA, S* sB, S* sC, S* sD, in
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// Lean binary32 sweeps for the register-staged tiles.  Same recurrences as
+// block_reduce / block_substitute, with pointers stepped by ld, the first and
+// last rows peeled, gamma, delta and alpha started at (0, 0, -1) so that the
+// first interior row needs no special case, and the pivot check folded into
+// z = fma(r, 0, z) (nan once a reciprocal is infinite or nan), tested once
+// per block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_lean(float x, float& e) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  e = fmaf(-x, y, 1.0f);
+  return y;
+}
+
+// Stage 1 without kept coefficients (len >= 3 handled here, shorter blocks by
+// block_reduce).  The forward values overwrite the a, c, d rows.
+__device__ __forceinline__ IfaceRows lean_reduce(float* A, float* B, float* Cc, float* D, int ld,
+                                                 const BlockInfo& bi, unsigned* status) {
+  const int len = bi.len;
+  if (len < 3) return block_reduce<float, float, false>(A, B, Cc, D, ld, bi, status);
+  if (bi.last) Cc[(len - 1) * ld] = 0.0f;
+  const float a0 = bi.first ? 0.0f : A[0], b0 = B[0], c0 = Cc[0], d0 = D[0];
+  float gam = 0.0f, del = 0.0f, alp = -1.0f, z = 0.0f;
+  float *pa = A + ld, *pb = B + ld, *pc = Cc + ld, *pd = D + ld;
+  for (int j = 1; j < len; ++j) {
+    const float a = *pa, b = *pb, c = *pc, d = *pd;
+    float e;
+    const float x = fmaf(-a, gam, b);
+    const float y = rcp_lean(x, e);
+    const float r = fmaf(y, e, y);
+    const float cy = c * y;
+    gam = fmaf(cy, e, cy);
+    z = fmaf(r, 0.0f, z);
+    const float q = a * r;
+    del = fmaf(-q, del, d * r);
+    alp = -q * alp;
+    *pa = alp;
+    *pc = gam;
+    *pd = del;
+    pa += ld; pb += ld; pc += ld; pd += ld;
+  }
+  IfaceRows out;
+  out.a1 = widen(alp);
+  out.b1 = 1.0;
+  out.c1 = widen(gam);
+  out.d1 = widen(del);
+  // backward over rows len-2 .. 1
+  pa = A + (len - 2) * ld; pc = Cc + (len - 2) * ld; pd = D + (len - 2) * ld;
+  float ap = *pa, gp = *pc, dp = *pd;
+  for (int j = len - 3; j >= 1; --j) {
+    pa -= ld; pc -= ld; pd -= ld;
+    const float gj = *pc;
+    dp = fmaf(-gj, dp, *pd);
+    ap = fmaf(-gj, ap, *pa);
+    gp = -gj * gp;
+  }
+  out.a0 = widen(a0);
+  out.b0 = widen(fmaf(-c0, ap, b0));
+  out.c0 = widen(-c0 * gp);
+  out.d0 = widen(fmaf(-c0, dp, d0));
+  if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+  return out;
+}
+
+// Stage 3 interior solve (len >= 3 here, shorter blocks are trivial): gamma
+// goes to G (which may be the c plane when c is not needed afterwards), x to D.
+__device__ __forceinline__ void lean_substitute(const float* A, const float* B, const float* Cc, float* D, float* G,
+                                                int ld, int len, float yl, float yr, unsigned* status) {
+  if (len <= 0) return;
+  if (len >= 3) {
+    // the known interface values move to the right-hand sides of rows 1 and len-2
+    const float c_end = Cc[(len - 2) * ld];
+    D[ld] = fmaf(-A[ld], yl, D[ld]);
+    D[(len - 2) * ld] = fmaf(-c_end, yr, D[(len - 2) * ld]);
+    float gam = 0.0f, del = 0.0f, z = 0.0f;
+    const float *pa = A + ld, *pb = B + ld, *pc = Cc + ld;
+    float *pd = D + ld, *pg = G + ld;
+    for (int j = 1; j < len - 2; ++j) {
+      const float a = *pa, b = *pb, c = *pc, d = *pd;
+      float e;
+      const float x = fmaf(-a, gam, b);
+      const float y = rcp_lean(x, e);
+      const float r = fmaf(y, e, y);
+      const float cy = c * y;
+      gam = fmaf(cy, e, cy);
+      z = fmaf(r, 0.0f, z);
+      del = fmaf(-a * r, del, d * r);
+      *pg = gam;
+      *pd = del;
+      pa += ld; pb += ld; pc += ld; pd += ld; pg += ld;
+    }
+    {  // row len-2: no coupling to the right any more
+      float e;
+      const float a = *pa;
+      const float x = fmaf(-a, gam, *pb);
+      const float y = rcp_lean(x, e);
+      const float r = fmaf(y, e, y);
+      z = fmaf(r, 0.0f, z);
+      del = fmaf(-a * r, del, *pd * r);
+      *pd = del;
+    }
+    float xn = del;
+    for (int j = len - 3; j >= 1; --j) {
+      pd -= ld; pg -= ld;
+      xn = fmaf(-*pg, xn, *pd);
+      *pd = xn;
+    }
+    if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+  }
+  D[0] = yl;
+  if (len >= 2) D[(len - 1) * ld] = yr;
+}
+
 // Interior solve of one block with x[L] = yl and x[R] = yr known (Stage 3,
 // the "substitute and solve the rest" step).  Reads a, b, c, d from the
 // tiles (type S), leaves x in the D tile, uses the C tile as scratch.
@@ -179,7 +295,11 @@ __global__ void __launch_bounds__(256) k_stage1(const S* __restrict__ a, const S
   }
   __syncthreads();
   if (t < nb) {
-    const IfaceRows r = block_reduce<C, C, KEEP>(sA + t, sB + t, sC + t, sD + t, ld, bi, status);
+    IfaceRows r;
+    if constexpr (std::is_same<C, float>::value && !KEEP)
+      r = lean_reduce(sA + t, sB + t, sC + t, sD + t, ld, bi, status);
+    else
+      r = block_reduce<C, C, KEEP>(sA + t, sB + t, sC + t, sD + t, ld, bi, status);
     write_iface(k0 + t, r, ra, rb, rc, rd);
   }
   if constexpr (KEEP) {
@@ -294,7 +414,10 @@ __global__ void __launch_bounds__(256) k_stage3_resolve(const S* __restrict__ a,
   __syncthreads();
   if (t < nb) {
     const double2 v = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));
-    block_substitute<C, C>(sA + t, sB + t, sC + t, sD + t, ld, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
+    if constexpr (std::is_same<C, float>::value)
+      lean_substitute(sA + t, sB + t, sC + t, sD + t, sC + t, ld, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
+    else
+      block_substitute<C, C>(sA + t, sB + t, sC + t, sD + t, ld, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
   }
   __syncthreads();
   {
@@ -432,13 +555,13 @@ __global__ void __launch_bounds__(256) k_refine_pass_cta(const double* __restric
   // ---- 2. binary32 interior solve of the correction, binary64 update ----
   if (t < nb && len > 0) {
     const double2 yv = *reinterpret_cast<const double2*>(yc + 2 * k);
-    const float yl = __double2float_rn(yv.x), yr = __double2float_rn(yv.y);
+    const float yl = narrow(yv.x), yr = narrow(yv.y);
     if (len >= 3) {
       float gam = 0.f, del = 0.f;
       for (int j = 1; j <= len - 2; ++j) {
-        const float aj = __double2float_rn(A[j * ld]), bj = __double2float_rn(Bp[j * ld]),
-                    cj = __double2float_rn(Cp[j * ld]);
-        float rj = __double2float_rn(R[j * ld]);
+        const float aj = narrow(A[j * ld]), bj = narrow(Bp[j * ld]),
+                    cj = narrow(Cp[j * ld]);
+        float rj = narrow(R[j * ld]);
         if (j == 1) rj = fmaf(-aj, yl, rj);
         if (j == len - 2) rj = fmaf(-cj, yr, rj);
         const float den = (j == 1) ? bj : fmaf(-aj, gam, bj);

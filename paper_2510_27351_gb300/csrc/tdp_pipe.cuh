@@ -339,13 +339,13 @@ __global__ void __launch_bounds__(128) k_refine_pass(const double* __restrict__ 
     // ---- 2. binary32 interior solve of the correction, binary64 update ----
     if (lane < tr.nb && len > 0) {
       const double2 yv = *reinterpret_cast<const double2*>(yc + 2 * k);
-      const float yl = __double2float_rn(yv.x), yr = __double2float_rn(yv.y);
+      const float yl = narrow(yv.x), yr = narrow(yv.y);
       if (len >= 3) {
         float gam = 0.f, del = 0.f;
         for (int j = 1; j <= len - 2; ++j) {
-          const float aj = __double2float_rn(A[j * ld]), bj = __double2float_rn(Bp[j * ld]),
-                      cj = __double2float_rn(Cp[j * ld]);
-          float rj = __double2float_rn(R[j * ld]);
+          const float aj = narrow(A[j * ld]), bj = narrow(Bp[j * ld]),
+                      cj = narrow(Cp[j * ld]);
+          float rj = narrow(R[j * ld]);
           if (j == 1) rj = fmaf(-aj, yl, rj);
           if (j == len - 2) rj = fmaf(-cj, yr, rj);
           const float den = (j == 1) ? bj : fmaf(-aj, gam, bj);

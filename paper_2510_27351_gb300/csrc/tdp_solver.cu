@@ -16,6 +16,7 @@
 #include "tdp_vtile.cuh"
 #include "tdp_coop.cuh"
 #include "tdp_wtile.cuh"
+#include "tdp_refine.cuh"
 
 namespace tdp {
 
@@ -805,6 +806,54 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
     stage3_resolve<T, T, MAPPED>(ctx, A, B, Cc, D, n, s, m, blk, y, (T*)x);
   } else if (refine_fused<MAPPED>(ctx, a, b, c, d, x, n, s, m, blk, ra, rb, rc, rd, y, refine_iters)) {
     // binary32 eliminations, binary64 residual and correction, one fused pass per correction
+  } else if (ctx.refine3 && refine_iters >= 1) {
+    // three passes for the solve and its first correction (tdp_refine.cuh), then
+    // separate kernels for any further correction
+    const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
+    double* X = (double*)x;
+    float* rr = ctx.ar->take<float>(n);
+    double* r = ctx.ar->take<double>(refine_iters > 1 ? n : 1);
+    double* dx = ctx.ar->take<double>(refine_iters > 1 ? n : 1);
+    stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                         (float*)nullptr, (float*)nullptr);
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      size_t smem;
+      const int T = pick_threads(ctx, s, 5, 4, MAPPED, &smem);
+      auto kern = k_refine_mid<MAPPED>;
+      allow_smem(kern);
+      pre_launch(ctx, "refine_mid");
+      kern<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(A, B, Cc, D, X, rr, n, s, magic_for(s), m, blk, edge,
+                                                               y, ra, rb, rc, rd, ctx.status);
+      post_launch(ctx, "refine pass 2");
+    }
+    solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      size_t smem;
+      const int T = pick_threads(ctx, s, 4, 4, MAPPED, &smem);
+      auto kern = k_refine_last<MAPPED>;
+      allow_smem(kern);
+      pre_launch(ctx, "refine_last");
+      kern<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(A, B, Cc, rr, X, n, s, magic_for(s), m, blk, y,
+                                                               ctx.status);
+      post_launch(ctx, "refine pass 3");
+    }
+    for (int it = 1; it < refine_iters; ++it) {
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "residual_f64");
+        k_residual<MAPPED><<<grid_for(n, 256), 256, 0, ctx.stream>>>(A, B, Cc, D, X, r, n, edge);
+        post_launch(ctx, "residual");
+      }
+      stage1<double, float, MAPPED, false>(ctx, A, B, Cc, r, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
+                                           (float*)nullptr, (float*)nullptr);
+      solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+      stage3_resolve<double, float, MAPPED>(ctx, A, B, Cc, r, n, s, m, blk, y, dx);
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "update_f64");
+        k_add<<<grid_for(n, 256), 256, 0, ctx.stream>>>(X, dx, n);
+        post_launch(ctx, "update");
+      }
+    }
   } else {
     // binary32 eliminations, binary64 residual and correction (separate kernels)
     const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;

@@ -31,13 +31,17 @@ __device__ __forceinline__ void owner(const TileGeom& g, int p, int& t, int& j) 
 }
 
 // Load NA arrays of storage type S (n_arr valid elements each) for rows
-// [ts, te) into shared tiles of compute type C.
+// [ts, te) into shared tiles of compute type C.  When blocks start on vector
+// boundaries (one system, s a multiple of V) a vector never straddles two
+// blocks: its owner is computed once and its elements go to consecutive rows
+// of that block.
 template <typename S, typename C, bool MAPPED, int NA>
 __device__ __forceinline__ void tile_load(const TileGeom& g, const S* const* src, C* const* dst, int64_t n_arr) {
   constexpr int V = Vec<S>::W;
   constexpr int U = 4;  // chunks in flight per thread per iteration
   const int64_t q0 = g.ts / V, q1 = (g.te + V - 1) / V;
   const int64_t step = blockDim.x;
+  const bool whole = !MAPPED && g.s % V == 0 && g.ts % V == 0;
   for (int64_t qb = q0 + threadIdx.x; qb < q1; qb += U * step) {
     Vec<S> v[U][NA];
 #pragma unroll
@@ -59,6 +63,16 @@ __device__ __forceinline__ void tile_load(const TileGeom& g, const S* const* src
       const int64_t q = qb + u * step;
       if (q >= q1) continue;
       const int64_t base = q * V;
+      if (whole && base + V <= g.te) {
+        int t, j;
+        owner<false>(g, int(base - g.ts), t, j);
+        const int idx = j * g.ld + t;
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+#pragma unroll
+          for (int i = 0; i < NA; ++i) dst[i][idx + e * g.ld] = cvt<C>(v[u][i].v[e]);
+        continue;
+      }
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         const int64_t pg = base + e;
@@ -80,8 +94,22 @@ template <typename C, typename D, bool MAPPED, int NA>
 __device__ __forceinline__ void tile_store(const TileGeom& g, const C* const* src, D* const* dst) {
   constexpr int V = Vec<D>::W;
   const int64_t q0 = g.ts / V, q1 = (g.te + V - 1) / V;
+  const bool whole = !MAPPED && g.s % V == 0 && g.ts % V == 0;
   for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     const int64_t base = q * V;
+    if (whole && base + V <= g.te) {
+      int t, j;
+      owner<false>(g, int(base - g.ts), t, j);
+      const int idx = j * g.ld + t;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        Vec<D> w;
+#pragma unroll
+        for (int e = 0; e < V; ++e) w.v[e] = cvt<D>(src[i][idx + e * g.ld]);
+        stg16<D>(dst[i] + base, w);
+      }
+      continue;
+    }
     Vec<D> v[NA];
 #pragma unroll
     for (int e = 0; e < V; ++e) {

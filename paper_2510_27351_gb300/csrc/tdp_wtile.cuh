@@ -182,7 +182,7 @@ __device__ __forceinline__ void wsubstitute_full(S* pa, S* pb, S* pc, S* pd, int
   constexpr int V = Vec<S>::W;
   using SL = Slot<S, float>;
   const int G = s / V;
-  const float fl = float(yl), fr = float(yr);
+  const float fl = narrow(yl), fr = narrow(yr);
   if (s >= 3) {
     // the known interface values move to the right-hand sides of rows 1 and s-2
     pd[1] = cvt<S>(fmaf(-cvt<float>(pa[1]), fl, cvt<float>(pd[1])));
@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(128) k_stage3_resolve_w(const S* __restrict__ 
       wsubstitute_full<S>(pa, pa + plane, pa + 2 * plane, pa + 3 * plane, s, v.x, v.y, z);
       if (!(z == 0.0f)) flag(status, ST_SINGULAR);
     } else {
-      vblock_substitute<S, float>(pa, pa + plane, pa + 2 * plane, pa + 3 * plane, 1, 0, l.len, float(v.x),
-                                  float(v.y), status);
+      vblock_substitute<S, float>(pa, pa + plane, pa + 2 * plane, pa + 3 * plane, 1, 0, l.len, narrow(v.x),
+                                  narrow(v.y), status);
     }
     wstore<S>(l, pa + 3 * plane, x);
   });
