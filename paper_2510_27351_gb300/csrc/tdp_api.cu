@@ -79,9 +79,9 @@ struct Knob {
   std::atomic<int> v;
 };
 Knob g_knobs[10] = {
-    {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {32}},
-    {"TDP_S_TAIL", 3, 256, {16}},                          {"TDP_VTILE", 0, 1, {1}},
-    {"TDP_COOP", 0, 1, {0}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
+    {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
+    {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
+    {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
     {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
     {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
 };

@@ -34,15 +34,15 @@ struct Ctx {
   bool dry = false;            // size the workspace only, launch nothing
   cudaError_t err = cudaSuccess;
   int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
-  int s_rec = 32;              // sub-system size inside the interface-system recursion
+  int s_rec = 16;              // sub-system size inside the interface-system recursion
   bool pipeline = false;       // warp-tile cp.async pipeline with element copies (TDP_PIPELINE=1)
   bool wtile = false;          // warp-owned bulk-copy tiles (TDP_WTILE=1)
   bool refine3 = true;         // three fused passes for a solve and its first correction (TDP_REFINE3=0 off)
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
-  bool coop = false;           // small interface levels in one cooperative launch (TDP_COOP=1)
-  int s_tail = 16;             // sub-system size inside that launch (TDP_S_TAIL)
+  bool coop = true;            // small interface levels in one cooperative launch (TDP_COOP=0 off)
+  int s_tail = 8;              // sub-system size inside that launch (TDP_S_TAIL)
   bool fused_refine = false;   // one fused pass per refinement correction (TDP_FUSED_REFINE=1)
   std::string msg;
   void fail(cudaError_t e, const char* where) {
