@@ -142,6 +142,18 @@ def dist_setup():
     return world, rank, local
 
 
+def weak_value(n_per_rank, world, ms_max):
+    """Whole-job unknowns/s: every rank solved its own n_per_rank unknowns in
+    at most ms_max milliseconds."""
+    return world * n_per_rank / (ms_max * 1e-3)
+
+
+def run_reference_guard(rank, fn):
+    """The reference arm runs on rank 0 only; the other ranks return at once."""
+    if rank == 0:
+        fn()
+
+
 def barrier_max(value, world, device):
     """Barrier, then the maximum of ``value`` over ranks."""
     if world == 1:
@@ -158,8 +170,10 @@ def barrier_max(value, world, device):
 # reference arm: the CPU oracle as it stands
 # ---------------------------------------------------------------------------
 def run_reference(args, world, rank):
-    if rank != 0:
-        return
+    run_reference_guard(rank, lambda: _reference_line(args))
+
+
+def _reference_line(args):
     import oracle
 
     S = W.single(N_MAIN, seed=0)
@@ -285,7 +299,7 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
     ms = barrier_max(ms, world, device)
     clocks = clk.summary()
-    value = world * N_MAIN / (ms * 1e-3)
+    value = weak_value(N_MAIN, world, ms)
     gpu_launches = launches_b - launches_a
 
     # ---- roofline of the dominant kernel (library event timing of the same step) ----
