@@ -116,6 +116,32 @@ int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, c
  * paper's interval rule (Sec. II-D).  Never fails: returns a valid s >= 2. */
 int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype);
 
+/* Number R of recursive steps of the partition method (Sec. III-A: a
+ * 1-nearest-neighbour model for the optimum number of recursive steps).
+ * 1-NN over (log2 n, log2 batch) in the recursion-depth table of the given
+ * precision (ties to the larger R): the table loaded by tdp_load_rtable, else
+ * the built-in one measured on GB300, else the intervals of the paper's table
+ * of optimum R (R = 0 up to 2.2e6 unknowns, 1 up to 4.8e6, 2 up to 9.6e6,
+ * 3 above).  Used by the solves when the tuning key TDP_TUNE_RECURSION is 1.
+ * Returns -1 for n < 1, batch < 1 or an unknown dtype. */
+int32_t tdp_predict_r(int64_t n, int32_t batch, tdp_dtype dtype);
+
+/* Load a recursion-depth table: a text file of rows "dtype n batch R"
+ * ('#' starts a comment), R in [0, 12].  The empty string "" restores the
+ * built-in table.  TDP_EINVAL for an unreadable file or a bad row (the
+ * current table is kept). */
+int tdp_load_rtable(const char* path);
+
+/* Sub-system sizes of the R recursive steps the paper's schedule (Sec. III-B)
+ * uses for one system of n unknowns partitioned with sub-system size s: step
+ * 1 uses 10 when R >= 2, every other step the size model (tdp_predict_s,
+ * binary64) applied to the interface system it partitions; steps stop early
+ * once the interface system has at most 64 rows or would form one block.
+ * R < 0 means the predicted R (tdp_predict_r).  Writes at most cap sizes to
+ * the HOST array m_out and returns how many steps there are, or -1 for bad
+ * arguments.  Host only. */
+int32_t tdp_recursion_plan(int64_t n, int32_t s, int32_t R, tdp_dtype dtype, int32_t* m_out, int32_t cap);
+
 /* The same size model evaluated on the device, one system per thread: s_out[j]
  * (DEVICE array of batch int32) receives the predicted s of system j of
  * the batch described by the DEVICE offsets (batch+1 int64), with the batch
@@ -164,6 +190,9 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline (element copies) */
 #define TDP_TUNE_WTILE 8        /* 1: warp-owned bulk-copy (TMA) tiles for binary32 sweeps of single systems */
 #define TDP_TUNE_REFINE3 9      /* 1: TDP_F32_REFINE runs its solve and first correction as three fused passes */
+#define TDP_TUNE_RECURSION 10   /* 1: the interface system follows the paper's recursion schedule (Sec. III);
+                                   0: s = TDP_TUNE_S_REC levels down to 2^19 rows, then the one-launch tail */
+#define TDP_TUNE_R 11           /* number of recursive steps of that schedule, -1 = tdp_predict_r [-1, 12] */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

@@ -61,6 +61,11 @@ def _load() -> ctypes.CDLL:
     lib.tdp_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.tdp_predict_s_batched.argtypes = [P, I32, I32, P, P]
     lib.tdp_get_tuning.argtypes = [ctypes.c_int]
+    lib.tdp_predict_r.argtypes = [I64, I32, I32]
+    lib.tdp_predict_r.restype = I32
+    lib.tdp_load_rtable.argtypes = [ctypes.c_char_p]
+    lib.tdp_recursion_plan.argtypes = [I64, I32, I32, I32, P, I32]
+    lib.tdp_recursion_plan.restype = I32
     return lib
 
 
@@ -70,10 +75,11 @@ LIB = _load()
 SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_backward", "tdp_predict_s",
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
-           "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched")
+           "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
+           "tdp_load_rtable", "tdp_recursion_plan")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
- TUNE_WTILE, TUNE_REFINE3) = range(10)
+ TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R) = range(12)
 
 
 def _check(rc: int):
@@ -160,6 +166,23 @@ def tdp_predict_s_batched(offsets, batch, dtype, s_out, stream=None):
 
 def tdp_load_table(path: str):
     _check(LIB.tdp_load_table(path.encode()))
+
+
+def tdp_predict_r(n: int, batch: int = 1, dtype: int = F64) -> int:
+    return int(LIB.tdp_predict_r(int(n), int(batch), int(dtype)))
+
+
+def tdp_load_rtable(path: str):
+    _check(LIB.tdp_load_rtable(path.encode()))
+
+
+def tdp_recursion_plan(n: int, s: int, R: int = -1, dtype: int = F64) -> list:
+    """Sub-system sizes of the recursive steps of the paper's schedule (host only)."""
+    buf = (ctypes.c_int32 * 16)()
+    k = int(LIB.tdp_recursion_plan(int(n), int(s), int(R), int(dtype), ctypes.cast(buf, ctypes.c_void_p), 16))
+    if k < 0:
+        raise TdpError(1, "tdp_recursion_plan: bad arguments")
+    return [int(buf[i]) for i in range(k)]
 
 
 def tdp_reserve(total_n, batch, s, dtype, stream=None):

@@ -72,18 +72,21 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // TDP_COOP, TDP_FUSED_REFINE, TDP_TMA, TDP_PIPELINE, TDP_WTILE, TDP_REFINE3
 // (0/1 switches of the interleaved tiles, the one-launch tail, the fused
 // refinement passes, the TMA-staged tiles, the element-copy warp-tile
-// pipeline, the warp-owned bulk-copy tiles and the three-pass refinement).
+// pipeline, the warp-owned bulk-copy tiles and the three-pass refinement),
+// TDP_RECURSION (1: the paper's recursion schedule) and TDP_R (its number of
+// recursive steps, -1 = predicted).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[10] = {
+Knob g_knobs[12] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
     {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
     {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
     {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
+    {"TDP_RECURSION", 0, 1, {0}},                          {"TDP_R", -1, 12, {-1}},
 };
 std::once_flag g_knobs_once;
 
@@ -110,6 +113,8 @@ void tune_from_env(Ctx& ctx) {
   ctx.pipeline = g_knobs[TDP_TUNE_PIPELINE].v.load() != 0;
   ctx.wtile = g_knobs[TDP_TUNE_WTILE].v.load() != 0;
   ctx.refine3 = g_knobs[TDP_TUNE_REFINE3].v.load() != 0;
+  ctx.rec_mode = g_knobs[TDP_TUNE_RECURSION].v.load();
+  ctx.rec_force = g_knobs[TDP_TUNE_R].v.load();
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.
@@ -202,6 +207,34 @@ void ensure_table() {
   if (g_table_init) return;
   for (const Row& r : kBuiltinTable) g_table.push_back(r);
   g_table_init = true;
+}
+
+// Rows (dtype, n, batch, R) of the recursion-depth model; the built-in rows
+// come from the GB300 sweep of R.  Without rows for a dtype the intervals of
+// the paper's table of optimum recursive steps (Sec. III-A) are used.
+struct RRow {
+  int dt;
+  double n, batch;
+  int r;
+};
+
+#include "tdp_rtable.inc"
+
+std::vector<RRow> g_rtable;
+bool g_rtable_init = false;
+
+void ensure_rtable() {
+  if (g_rtable_init) return;
+  for (const RRow& r : kBuiltinRTable)
+    if (r.r >= 0) g_rtable.push_back(r);
+  g_rtable_init = true;
+}
+
+int r_interval_rule(double n) {
+  if (n <= 2.2e6) return 0;
+  if (n <= 4.8e6) return 1;
+  if (n <= 9.6e6) return 2;
+  return 3;
 }
 
 int interval_rule(double n) {
@@ -306,6 +339,54 @@ int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt) {
   }
   if (s < 2) s = interval_rule(double(n));
   return s;
+}
+
+int32_t predict_r(int64_t n, int32_t batch, tdp_dtype dt) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  ensure_rtable();
+  const double ln = std::log2(double(n < 1 ? 1 : n));
+  const double lb = std::log2(double(batch < 1 ? 1 : batch));
+  double best = 1e300;
+  int r = -1;
+  for (const RRow& row : g_rtable) {
+    if (row.dt != int(dt)) continue;
+    const double dn = std::log2(row.n) - ln, db = std::log2(row.batch) - lb;
+    const double dist = dn * dn + db * db;
+    if (dist < best || (dist == best && row.r > r)) {
+      best = dist;
+      r = row.r;
+    }
+  }
+  if (r < 0) r = r_interval_rule(double(n));
+  return r;
+}
+
+int load_rtable_file(const char* path) {
+  if (path[0] == '\0') {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    g_rtable.clear();
+    g_rtable_init = false;
+    ensure_rtable();
+    return TDP_OK;
+  }
+  std::ifstream in(path);
+  if (!in) return set_error(TDP_EINVAL, std::string("tdp_load_rtable: cannot open ") + path);
+  std::vector<RRow> rows;
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t h = line.find('#');
+    if (h != std::string::npos) line.resize(h);
+    std::istringstream ss(line);
+    RRow r;
+    if (!(ss >> r.dt >> r.n >> r.batch >> r.r)) continue;
+    if (r.dt < 0 || r.dt > 2 || r.n < 1 || r.batch < 1 || r.r < 0 || r.r > 12)
+      return set_error(TDP_EINVAL, "tdp_load_rtable: bad row: " + line);
+    rows.push_back(r);
+  }
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  g_rtable = rows;
+  g_rtable_init = true;
+  return TDP_OK;
 }
 
 int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels) {
@@ -421,6 +502,22 @@ int tdp_predict_s_batched(const int64_t* offsets, int32_t batch, tdp_dtype dtype
   if (dtype != TDP_F64 && dtype != TDP_F32 && dtype != TDP_F32_REFINE)
     return set_error(TDP_EINVAL, "tdp_predict_s_batched: unsupported dtype");
   return run(stream, "tdp_predict_s_batched", [&](Ctx& ctx) { predict_sizes(ctx, offsets, batch, dtype, s_out); });
+}
+
+int32_t tdp_predict_r(int64_t n, int32_t batch, tdp_dtype dtype) {
+  if (n < 1 || batch < 1 || int(dtype) < 0 || int(dtype) > 2) return -1;
+  return predict_r(n, batch, dtype);
+}
+
+int tdp_load_rtable(const char* path) {
+  if (!path) return set_error(TDP_EINVAL, "tdp_load_rtable: null path");
+  return load_rtable_file(path);
+}
+
+int32_t tdp_recursion_plan(int64_t n, int32_t s, int32_t R, tdp_dtype dtype, int32_t* m_out, int32_t cap) {
+  if (n < 1 || s < 2 || s > 1024 || R > 12 || int(dtype) < 0 || int(dtype) > 2 || cap < 0 || (cap > 0 && !m_out))
+    return -1;
+  return recursion_plan(n, 1, s, R, dtype, m_out, cap);
 }
 
 int32_t tdp_predict_s(int64_t n, int32_t batch, tdp_dtype dtype) {

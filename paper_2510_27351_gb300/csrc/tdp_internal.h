@@ -38,6 +38,11 @@ struct Ctx {
   bool pipeline = false;       // warp-tile cp.async pipeline with element copies (TDP_PIPELINE=1)
   bool wtile = false;          // warp-owned bulk-copy tiles (TDP_WTILE=1)
   bool refine3 = true;         // three fused passes for a solve and its first correction (TDP_REFINE3=0 off)
+  int rec_mode = 0;            // 1: the paper's recursion schedule for the interface system (TDP_RECURSION)
+  int rec_force = -1;          // its number of recursive steps; -1: predicted (TDP_R)
+  int64_t rec_n = 1;           // size, batch and dtype the recursion depth is predicted for
+  int32_t rec_batch = 1;
+  tdp_dtype rec_dt = TDP_F64;
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
@@ -84,6 +89,9 @@ bool checked_mode();
 
 // Predictor (host 1-NN over the loaded table; tdp_api.cu).
 int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);
+int32_t predict_r(int64_t n, int32_t batch, tdp_dtype dt);
+int load_rtable_file(const char* path);
+int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap);
 // Flattened table for the device-side predictor: rows of (log2 n, log2 batch, s) per dtype.
 int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels);
 

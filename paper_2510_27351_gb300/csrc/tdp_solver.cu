@@ -460,9 +460,61 @@ void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const do
   post_launch(ctx, "interface cooperative launch");
 }
 
+// Sub-system size of recursive step `level` (1-based) of R under the paper's
+// rule (Sec. III-B): the first step uses 10 when R >= 2, every other step the
+// size model applied to the interface system it partitions.
+int paper_level_size(int level, int R, int64_t M) {
+  int m = (level == 1 && R >= 2) ? 10 : int(predict_s(M, 1, TDP_F64));
+  return m < 3 ? 3 : m;
+}
+
+void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
+                     int64_t M);
+
+// The paper's recursive variant: R recursive steps, each a partition of the
+// current interface system with its own sub-system size, then the last
+// interface system solved directly on the device (one cooperative launch, or
+// one thread when it has at most 64 rows).
+void solve_interface_rec(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
+                         double* y, int64_t M, int level, int R) {
+  if (M <= 0) return;
+  const int s2 = (level <= R && M > kBaseRows) ? paper_level_size(level, R, M) : 0;
+  if (s2 == 0 || s2 >= M) {
+    if (M <= kBaseRows) {
+      double* scratch = ctx.ar->take<double>(M);
+      if (ctx.dry || ctx.err != cudaSuccess) return;
+      pre_launch(ctx, "interface_base");
+      k_thomas<double, double><<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, nullptr, 1, M, 0, 1, M, scratch,
+                                                          ctx.status);
+      post_launch(ctx, "interface base solve");
+    } else {
+      solve_interface_coop(ctx, ra, rb, rc, rd, y, M);
+    }
+    return;
+  }
+  const int64_t m2 = (M + s2 - 1) / s2;
+  double* ka = ctx.ar->take<double>(M);
+  double* kg = ctx.ar->take<double>(M);
+  double* kd = ctx.ar->take<double>(M);
+  double* ra2 = ctx.ar->take<double>(2 * m2);
+  double* rb2 = ctx.ar->take<double>(2 * m2);
+  double* rc2 = ctx.ar->take<double>(2 * m2);
+  double* rd2 = ctx.ar->take<double>(2 * m2);
+  double* y2 = ctx.ar->take<double>(2 * m2);
+  stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd,
+                                      "iface_stage1_f64");
+  solve_interface_rec(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2, level + 1, R);
+  stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f64");
+}
+
 void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
                      int64_t M) {
   if (M <= 0) return;
+  if (ctx.rec_mode == 1) {
+    const int R = ctx.rec_force >= 0 ? ctx.rec_force : int(predict_r(ctx.rec_n, ctx.rec_batch, ctx.rec_dt));
+    solve_interface_rec(ctx, ra, rb, rc, rd, y, M, 1, R);
+    return;
+  }
   if (ctx.coop && M > kBaseRows && M <= kCoopMax) {
     solve_interface_coop(ctx, ra, rb, rc, rd, y, M);
     return;
@@ -958,8 +1010,24 @@ BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
 // ---------------------------------------------------------------------------
 // Public drivers
 // ---------------------------------------------------------------------------
+int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap) {
+  if (R < 0) R = int(predict_r(n, batch, dt));
+  int64_t M = 2 * ((n + s - 1) / s);
+  int count = 0;
+  for (int level = 1; level <= R && M > kBaseRows && count < cap; ++level) {
+    const int m = paper_level_size(level, R, M);
+    if (m >= M) break;
+    m_out[count++] = m;
+    M = 2 * ((M + m - 1) / m);
+  }
+  return count;
+}
+
 void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
                   tdp_dtype dt, int refine_iters) {
+  ctx.rec_n = n;
+  ctx.rec_batch = 1;
+  ctx.rec_dt = dt;
   if (s > n) s = int(std::max<int64_t>(2, n));
   const int64_t m = (n + s - 1) / s;
   solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
@@ -967,6 +1035,9 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
 
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                    const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
+  ctx.rec_n = total_n;
+  ctx.rec_batch = batch;
+  ctx.rec_dt = dt;
   if (batch <= 0 || total_n <= 0) return;
   const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;
   if (s == 0) {
@@ -998,6 +1069,9 @@ void predict_sizes(Ctx& ctx, const int64_t* offsets, int32_t batch, tdp_dtype dt
 
 void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, const void* a, const void* b,
                    const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
+  ctx.rec_n = int64_t(batch) * n;
+  ctx.rec_batch = batch;
+  ctx.rec_dt = dt;
   if (batch <= 0 || n <= 0) return;
   const int64_t total = int64_t(batch) * n;
   int64_t* off = ctx.ar->take<int64_t>(batch + 1);
@@ -1044,6 +1118,9 @@ void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, c
 void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                     const void* c, const void* x, const void* g, void* ga, void* gb, void* gc, void* gd, int s,
                     tdp_dtype dt) {
+  ctx.rec_n = total_n;
+  ctx.rec_batch = batch;
+  ctx.rec_dt = dt;
   if (batch <= 0 || total_n <= 0) return;
   const size_t el = (dt == TDP_F32) ? 4 : 8;
   uint8_t* edge = ctx.ar->take<uint8_t>(total_n);
@@ -1099,6 +1176,9 @@ void thomas_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
 
 void solve_single_lean(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
                        int s, tdp_dtype dt) {
+  ctx.rec_n = n;
+  ctx.rec_batch = 1;
+  ctx.rec_dt = dt;
   if (s > n) s = int(std::max<int64_t>(2, n));
   const int64_t m = (n + s - 1) / s;
   double* ra = ctx.ar->take<double>(2 * m);

@@ -13,6 +13,17 @@ a second feature for batched solves).  The library's predictor
 
 The sweep appends one JSON line per (dtype, n, batch, s) so that a killed
 sweep resumes where it stopped.
+
+The number of recursive steps R of the paper's recursive variant (Sec. III)
+gets the same treatment: ``sweep-r`` times the paper's schedule for every R of
+a grid (and the library's default schedule, recorded as R = -1), ``rtable``
+writes the fastest R per size for ``tdp_predict_r``, ``evaluate-r`` reports the
+1-NN accuracy, the time lost against the fastest R and the comparison with the
+default schedule.
+
+    python -m paper_2510_27351_gb300.tune sweep-r --out sweep_r.jsonl
+    python -m paper_2510_27351_gb300.tune rtable --sweep sweep_r.jsonl --out table_r.txt --inc csrc/tdp_rtable.inc
+    python -m paper_2510_27351_gb300.tune evaluate-r --sweep sweep_r.jsonl
 """
 from __future__ import annotations
 
@@ -25,6 +36,7 @@ import sys
 from collections import defaultdict
 
 S_GRID = (4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 96, 128)
+R_GRID = (0, 1, 2, 3, 4, 5)
 DTYPES = {0: "f64", 1: "f32", 2: "f32_refine"}
 TOL = 0.05  # labels within 5 % of the fastest count as near-optimal
 
@@ -305,6 +317,167 @@ def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(
                     torch.cuda.empty_cache()
 
 
+# ---------------------------------------------------------------------------
+# number of recursive steps (Sec. III)
+# ---------------------------------------------------------------------------
+def _random_system(total, dt, g, dev):
+    import torch
+
+    st = torch.float32 if dt == 1 else torch.float64
+    a = torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1
+    b = torch.rand(total, generator=g, device=dev, dtype=st) * 4 + 4
+    c = torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1
+    d = torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1
+    return a, b, c, d
+
+
+def _time_ms(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def sweep_r(out, dtypes=(0, 2), log2_lo=14.0, log2_hi=28.0, step=0.5, reps=5, r_grid=R_GRID):
+    """Time one system per size with the paper's recursion schedule for every R
+    of r_grid, and with the default schedule (recorded as R = -1); s is the
+    size model's choice."""
+    import torch
+
+    import paper_2510_27351_gb300 as tdp
+
+    done = set()
+    if os.path.exists(out):
+        for r in load_sweep(out):
+            done.add((r["dtype"], r["n"], r["R"]))
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    sizes = []
+    x = log2_lo
+    while x <= log2_hi + 1e-9:
+        sizes.append(int(round(2 ** x)))
+        x += step
+    old = (tdp.tdp_get_tuning(tdp.TUNE_RECURSION), tdp.tdp_get_tuning(tdp.TUNE_R))
+    try:
+        with open(out, "a") as fh:
+            for n in sizes:
+                for dt in dtypes:
+                    todo = [r for r in (-1,) + tuple(r_grid) if (dt, n, r) not in done]
+                    if not todo:
+                        continue
+                    a, b, c, d = _random_system(n, dt, g, dev)
+                    xo = torch.empty_like(d)
+                    s = tdp.tdp_predict_s(n, 1, dt)
+                    it = 1 if dt == 2 else 0
+                    for r in todo:
+                        tdp.tdp_set_tuning(tdp.TUNE_RECURSION, 0 if r < 0 else 1)
+                        tdp.tdp_set_tuning(tdp.TUNE_R, max(r, -1))
+                        ms = _time_ms(lambda: tdp.tdp_solve(a, b, c, d, xo, n, s, dt, it),
+                                      reps if n >= (1 << 20) else 4 * reps)
+                        fh.write(json.dumps({"dtype": dt, "n": n, "batch": 1, "R": r, "s": s, "ms": ms}) + "\n")
+                        fh.flush()
+                    del a, b, c, d, xo
+                    torch.cuda.empty_cache()
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_RECURSION, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_R, old[1])
+
+
+def grouped_r(rows):
+    """{(dtype, batch): [(n, {R: ms}), ...]} sorted by n; R = -1 is the default schedule."""
+    acc = defaultdict(lambda: defaultdict(dict))
+    for r in rows:
+        acc[(r["dtype"], r["batch"])][r["n"]][r["R"]] = r["ms"]
+    return {k: sorted(v.items()) for k, v in acc.items()}
+
+
+def best_r(times):
+    """Fastest R >= 0 (ties to the larger R)."""
+    cand = {r: t for r, t in times.items() if r >= 0}
+    tmin = min(cand.values())
+    return max(r for r, t in cand.items() if t == tmin)
+
+
+def r_labels(series):
+    """Observed (fastest) and corrected R per size: the label correction of the
+    size model (within TOL of the fastest, trend-consistent) applied to the
+    times of the paper's schedule, R >= 0."""
+    times = [{r: t for r, t in tm.items() if r >= 0} for _, tm in series]
+    raw = [best_r(t) for t in times]
+    _, cor, rule = correct_relaxed(times)
+    return raw, cor, rule
+
+
+def build_rtable(rows):
+    out = []
+    for (dt, batch), series in sorted(grouped_r(rows).items()):
+        _, cor, _ = r_labels(series)
+        out += [(dt, n, batch, r) for (n, _), r in zip(series, cor)]
+    return out
+
+
+def write_rtable(table, path_txt=None, path_inc=None):
+    if path_txt:
+        with open(path_txt, "w") as fh:
+            fh.write("# dtype n batch R   (GB300 sweep of the number of recursive steps, corrected labels)\n")
+            for dt, n, b, r in table:
+                fh.write(f"{dt} {n} {b} {r}\n")
+    if path_inc:
+        with open(path_inc, "w") as fh:
+            fh.write("// Recursion-depth table (dtype, n, batch, R): the number of recursive steps per\n"
+                     "// size from the GB300 sweep written by paper_2510_27351_gb300/tune.py (within 5 %\n"
+                     "// of the fastest R, corrected towards the trend like the size model's labels).\n"
+                     "const RRow kBuiltinRTable[] = {\n")
+            for dt, n, b, r in table:
+                fh.write(f"    {{{dt}, {float(n)!r}, {float(b)!r}, {r}}},\n")
+            fh.write("};\n")
+
+
+def evaluate_r(rows, seed=0):
+    """Per dtype: shuffled 3:1 split keeping every R in training, 1-NN accuracy
+    and null accuracy (Sec. III-A), the time lost by the predicted R against the
+    fastest R, and the paper's schedule with the predicted R against the
+    library's default schedule, on the held-out sizes."""
+    report = {}
+    for (dt, batch), series in sorted(grouped_r(rows).items()):
+        sizes = [n for n, _ in series]
+        times = [t for _, t in series]
+        raw, lab, rule = r_labels(series)
+        idx = list(range(len(sizes)))
+        rng = random.Random(seed)
+        for _ in range(1000):
+            rng.shuffle(idx)
+            k = len(idx) // 4
+            test, train = idx[:k], idx[k:]
+            if set(lab[i] for i in train) == set(lab):
+                break
+        tr = [(sizes[i], batch, lab[i]) for i in train]
+        pred = {i: nearest(tr, sizes[i], batch) for i in test}
+        mode = max(set(lab), key=lab.count)
+        losses = [times[i][pred[i]] / times[i][raw[i]] - 1.0 for i in test]
+        vs_default = [times[i][pred[i]] / times[i][-1] for i in test if -1 in times[i]]
+        tr_raw = [(sizes[i], batch, raw[i]) for i in train]
+        report[f"{DTYPES.get(dt, dt)}/batch{batch}"] = {
+            "n_sizes": len(sizes), "labels_observed": dict(zip(map(str, sizes), raw)),
+            "labels": dict(zip(map(str, sizes), lab)), "correction_rule": rule,
+            "accuracy_observed": sum(nearest(tr_raw, sizes[i], batch) == raw[i] for i in test) / max(1, len(test)),
+            "accuracy": sum(pred[i] == lab[i] for i in test) / max(1, len(test)),
+            "null_accuracy": sum(lab[i] == mode for i in test) / max(1, len(test)),
+            "max_time_loss": max(losses) if losses else 0.0, "mean_time_loss": sum(losses) / max(1, len(losses)),
+            "predicted_over_default_mean": sum(vs_default) / max(1, len(vs_default)),
+            "best_over_default_all": {str(n): t[best_r(t)] / t[-1] for n, t in zip(sizes, times) if -1 in t},
+            "test_sizes": [sizes[i] for i in sorted(test)]}
+    return report
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -322,14 +495,33 @@ def main(argv=None):
     p.add_argument("--inc")
     p = sub.add_parser("evaluate")
     p.add_argument("--sweep", required=True)
+    p = sub.add_parser("sweep-r")
+    p.add_argument("--out", required=True)
+    p.add_argument("--dtypes", default="0,2")
+    p.add_argument("--lo", type=float, default=14.0)
+    p.add_argument("--hi", type=float, default=28.0)
+    p.add_argument("--step", type=float, default=0.5)
+    p.add_argument("--reps", type=int, default=5)
+    p = sub.add_parser("rtable")
+    p.add_argument("--sweep", required=True)
+    p.add_argument("--out")
+    p.add_argument("--inc")
+    p = sub.add_parser("evaluate-r")
+    p.add_argument("--sweep", required=True)
     args = ap.parse_args(argv)
     if args.cmd == "sweep":
         sweep(args.out, tuple(int(v) for v in args.dtypes.split(",")), args.lo, args.hi, args.step,
               tuple(int(v) for v in args.batches.split(",")), args.reps)
     elif args.cmd == "table":
         write_table(build_table(load_sweep(args.sweep)), args.out, args.inc)
-    else:
+    elif args.cmd == "evaluate":
         print(json.dumps(evaluate(load_sweep(args.sweep)), indent=1))
+    elif args.cmd == "sweep-r":
+        sweep_r(args.out, tuple(int(v) for v in args.dtypes.split(",")), args.lo, args.hi, args.step, args.reps)
+    elif args.cmd == "rtable":
+        write_rtable(build_rtable(load_sweep(args.sweep)), args.out, args.inc)
+    else:
+        print(json.dumps(evaluate_r(load_sweep(args.sweep)), indent=1))
 
 
 if __name__ == "__main__":

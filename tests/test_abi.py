@@ -100,3 +100,41 @@ def test_tuning_knobs_validate_and_round_trip():
         assert tdp.tdp_get_tuning(tdp.TUNE_S_REC) == 16
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_S_REC, old)
+
+
+def test_recursion_depth_model_and_plan_match_the_oracle(tmp_path):
+    """Host-only: tdp_predict_r without table rows follows the paper's
+    intervals of optimum R, and tdp_recursion_plan follows the paper's rule
+    for the sizes of the recursive steps (the oracle gets the library's size
+    model as its size predictor, so only the rule is compared)."""
+    import paper_2510_27351_gb300 as tdp
+    from oracle import predictor as P
+
+    gold = os.path.join(ROOT, "tests", "golden")
+    rule = [(int(float(r[0])), int(r[1])) for r in P.load_table(os.path.join(gold, "interval_rule_R.txt"))]
+    empty = tmp_path / "empty.txt"
+    empty.write_text("# no rows\n")
+    tdp.tdp_load_rtable(str(empty))
+    try:
+        for n in (1, 1000, 1e5, 2.2e6, 2.25e6, 2.3e6, 4.8e6, 4.9e6, 5e6, 9.6e6, 9.7e6, 1e7, 1e8, 1 << 28):
+            assert tdp.tdp_predict_r(int(n)) == P.interval_rule_r(int(n), rule), n
+    finally:
+        tdp.tdp_load_rtable("")
+    p = tmp_path / "r.txt"
+    p.write_text("0 1048576 1 2\n0 67108864 1 4\n")
+    tdp.tdp_load_rtable(str(p))
+    try:
+        assert tdp.tdp_predict_r(1 << 20) == 2 and tdp.tdp_predict_r(1 << 26) == 4
+        assert tdp.tdp_predict_r(1 << 23) == 4  # equal log2 distance: the larger R
+        bad = tmp_path / "bad.txt"
+        bad.write_text("0 1024 1 13\n")
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_load_rtable(str(bad))
+    finally:
+        tdp.tdp_load_rtable("")
+    pred = lambda M: tdp.tdp_predict_s(M, 1, tdp.F64)  # noqa: E731
+    for n in (100, 5000, 1 << 20, 4_500_000, 1 << 26):
+        for s in (2, 8, 24, 64):
+            for R in range(6):
+                assert tdp.tdp_recursion_plan(n, s, R) == P.recursive_sizes(n, s, R, pred), (n, s, R)
+    assert tdp.LIB.tdp_recursion_plan(0, 8, 1, 0, 0, 0) == -1

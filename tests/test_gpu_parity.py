@@ -330,3 +330,36 @@ def test_warp_bulk_tiles(tdp, code):
                 assert e <= TOL[code], (n, s, e)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_WTILE, old)
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_paper_recursion_schedule(tdp, code):
+    """The recursive variant (Sec. III) with R forced to 0..5 and predicted:
+    R recursive steps with the paper's sub-system sizes, then the last
+    interface system solved directly; every R gives x = A^-1 d."""
+    import torch
+
+    old = (tdp.tdp_get_tuning(tdp.TUNE_RECURSION), tdp.tdp_get_tuning(tdp.TUNE_R))
+    tdp.tdp_set_tuning(tdp.TUNE_RECURSION, 1)
+    try:
+        for n in (1000, 100_003, 1 << 20):
+            S = W.single(n, seed=n + 3)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for R in (-1, 0, 1, 2, 3, 5):
+                tdp.tdp_set_tuning(tdp.TUNE_R, R)
+                for s in (4, 8, 32):
+                    e = oracle.rel_err(_solve(tdp, S, s, code), ref)
+                    assert e <= TOL[code], (n, R, s, e)
+        Sb = W.batched(64, 64, 65536, seed=8)
+        refb = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        dt = torch.float32 if code == 1 else torch.float64
+        a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+        for R in (0, 2):
+            tdp.tdp_set_tuning(tdp.TUNE_R, R)
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(dev(Sb.offsets), Sb.batch, Sb.n, a, b, c, d, x, 0, code, 1 if code == 2 else 0)
+            torch.cuda.synchronize()
+            assert oracle.rel_err(host(x), refb) <= TOL[code], R
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_RECURSION, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_R, old[1])

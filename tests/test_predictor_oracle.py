@@ -87,3 +87,50 @@ def test_label_correction_reproduces_table4():
     assert all(x <= y for x, y in zip(corrected, corrected[1:]))
     for t, s in zip(times, corrected):
         assert t[s] <= 1.05 * min(t.values())
+
+
+def _table_r():
+    rows = P.load_table(os.path.join(GOLD, "table_opt_R.txt"))
+    return [int(float(r[0])) for r in rows], [int(r[1]) for r in rows]
+
+
+def _rule_r():
+    return [(int(float(r[0])), int(r[1])) for r in P.load_table(os.path.join(GOLD, "interval_rule_R.txt"))]
+
+
+def test_interval_rule_r_reproduces_table_of_optimum_r():
+    sizes, labels = _table_r()
+    rule = _rule_r()
+    assert [P.interval_rule_r(n, rule) for n in sizes] == labels
+    assert P.interval_rule_r(2_250_000, rule) == 1  # between two intervals: the larger R
+    assert P.interval_rule_r(1e9, rule) == 3
+
+
+def test_r_knn_reproduces_the_intervals():
+    """Sec. III-A: a 1-NN model over the listed sizes; inside every interval of
+    the table it returns that interval's R, and it reproduces its training
+    labels.  (Held-out accuracy depends on the split: sizes at an interval's
+    edge have their nearest neighbour across the edge.)"""
+    sizes, labels = _table_r()
+    assert [P.knn_predict(sizes, labels, n) for n in sizes] == labels
+    probes = {150_000: 0, 1_500_000: 0, 2_450_000: 1, 3_500_000: 1, 6_500_000: 2, 9_000_000: 2, 3e7: 3, 5e8: 3}
+    for n, r in probes.items():
+        assert P.knn_predict(sizes, labels, n) == r, n
+
+
+def test_recursive_sizes_follow_the_rule():
+    """Sec. III-B: step 1 uses 10 when R >= 2; every other step uses the size
+    model on the interface system it partitions (here a stub: 32 below 2^20
+    rows, 64 above); each step turns M rows into 2 ceil(M / m)."""
+    stub = lambda M: 32 if M < (1 << 20) else 64  # noqa: E731
+    n, s = 1 << 24, 16
+    M1 = 2 * (n // s)  # 2^21 rows
+    assert P.recursive_sizes(n, s, 0, stub) == []
+    assert P.recursive_sizes(n, s, 1, stub) == [64]  # R = 1: the model on M1
+    assert P.recursive_sizes(n, s, 2, stub) == [10, 32]  # 2 ceil(2^21 / 10) = 419432 rows < 2^20
+    sizes = P.recursive_sizes(n, s, 8, stub)
+    M = M1
+    for m in sizes:
+        M = 2 * -(-M // m)
+    assert sizes[0] == 10 and all(m in (32, 64) for m in sizes[1:]) and M <= 64
+    assert len(sizes) < 8  # stops once the interface system has at most 64 rows

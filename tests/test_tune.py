@@ -82,3 +82,26 @@ def test_evaluate_protocol_on_synthetic_sweep():
     assert rep["max_time_loss"] <= 0.25
     table = tune.build_table(rows)
     assert len(table) == 37 and all(r[3] in (8, 16, 32) for r in table)
+
+
+def test_recursion_depth_table_and_evaluation():
+    """tune.py's R pipeline on synthetic timings: the fastest R per size (ties
+    to the larger R, the default schedule R = -1 excluded), and an evaluation
+    whose losses are measured against that fastest R."""
+    from paper_2510_27351_gb300 import tune
+
+    rows = []
+    for k, n in enumerate([1 << e for e in range(14, 26)]):
+        best = 0 if n < (1 << 18) else 1 if n < (1 << 22) else 3
+        for r in (-1, 0, 1, 2, 3):
+            ms = 1.0 + abs(r - best) * 0.1 if r >= 0 else 1.05
+            if r == best + 1 and best == 0:
+                ms = 1.0  # a tie: the larger R wins
+            rows.append({"dtype": 0, "n": n, "batch": 1, "R": r, "s": 8, "ms": ms})
+    table = tune.build_rtable(rows)
+    lab = {n: r for _, n, _, r in table}
+    assert lab[1 << 14] == 1 and lab[1 << 20] == 1 and lab[1 << 24] == 3
+    rep = tune.evaluate_r(rows)["f64/batch1"]
+    assert rep["n_sizes"] == 12 and 0.0 <= rep["accuracy"] <= 1.0
+    assert rep["mean_time_loss"] >= 0.0
+    assert all(abs(v - 1.0 / 1.05) < 1e-12 for v in rep["best_over_default_all"].values())
