@@ -84,6 +84,23 @@ int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, co
                       const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
                       void* stream);
 
+/* Constant-coefficient systems (the implicit step of the heat equation and
+ * other alternating-direction schemes; not in the paper): `batch` systems of n
+ * unknowns whose rows all read  a x[i-1] + b x[i] + c x[i+1] = d[i]  (a of a
+ * system's first row and c of its last row are ignored).  d and x are
+ * DEVICE arrays addressed like tdp_solve_strided: element i of system j at
+ * j*sys_stride + i*elem_stride (in elements, both >= 1); the systems must not
+ * overlap: elem_stride >= batch*sys_stride (interleaved) or
+ * sys_stride >= n*elem_stride (one after another).  Pointers aligned to their
+ * element; x must not alias d.  The partition method with the coefficient
+ * part of Stage 1 (pivots, multipliers, spike and backward coefficients)
+ * computed once per call for a block of s rows; s in [2, 512] or 0 for the
+ * size model.  Moves 3 words per unknown (d twice, x once); dtype and
+ * refine_iters as tdp_solve. */
+int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_t n, int32_t batch,
+                    int64_t sys_stride, int64_t elem_stride, int32_t s, tdp_dtype dtype, int32_t refine_iters,
+                    void* stream);
+
 /* Solve `batch` systems of n unknowns each with arbitrary element strides:
  * element i of system j lives at index  j*sys_stride + i*elem_stride  of each
  * array (in elements).  sys_stride = n, elem_stride = 1 is a contiguous batch;

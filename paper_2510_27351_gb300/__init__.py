@@ -61,6 +61,8 @@ def _load() -> ctypes.CDLL:
     lib.tdp_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.tdp_predict_s_batched.argtypes = [P, I32, I32, P, P]
     lib.tdp_get_tuning.argtypes = [ctypes.c_int]
+    lib.tdp_solve_const.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, I64, I32, I64, I64,
+                                     I32, I32, I32, P]
     lib.tdp_predict_r.argtypes = [I64, I32, I32]
     lib.tdp_predict_r.restype = I32
     lib.tdp_load_rtable.argtypes = [ctypes.c_char_p]
@@ -76,7 +78,7 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
-           "tdp_load_rtable", "tdp_recursion_plan")
+           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
  TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R) = range(12)
@@ -166,6 +168,11 @@ def tdp_predict_s_batched(offsets, batch, dtype, s_out, stream=None):
 
 def tdp_load_table(path: str):
     _check(LIB.tdp_load_table(path.encode()))
+
+
+def tdp_solve_const(a, b, c, d, x, n, batch, sys_stride, elem_stride, s, dtype, refine_iters=0, stream=None):
+    _check(LIB.tdp_solve_const(float(a), float(b), float(c), _ptr(d), _ptr(x), int(n), int(batch), int(sys_stride),
+                               int(elem_stride), int(s), int(dtype), int(refine_iters), _stream(stream)))
 
 
 def tdp_predict_r(n: int, batch: int = 1, dtype: int = F64) -> int:

@@ -465,6 +465,31 @@ int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, co
   });
 }
 
+int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_t n, int32_t batch,
+                    int64_t sys_stride, int64_t elem_stride, int32_t s, tdp_dtype dtype, int32_t refine_iters,
+                    void* stream) {
+  const char* fn = "tdp_solve_const";
+  if (batch < 1) return set_error(TDP_EINVAL, std::string(fn) + ": batch must be >= 1");
+  if (s != 0 && (s < 2 || s > 512)) return set_error(TDP_EINVAL, std::string(fn) + ": s must be 0 or in [2, 512]");
+  int rc = check_common(n, 0, dtype, refine_iters, fn);
+  if (rc) return rc;
+  if (sys_stride < 1 || elem_stride < 1)
+    return set_error(TDP_EINVAL, std::string(fn) + ": strides must be >= 1");
+  // systems must not overlap: interleaved (elem_stride >= batch * sys_stride)
+  // or one after another (sys_stride >= n * elem_stride)
+  if (!(elem_stride >= int64_t(batch) * sys_stride || sys_stride >= n * elem_stride))
+    return set_error(TDP_EINVAL, std::string(fn) + ": strides make systems overlap");
+  const size_t el = dtype == TDP_F32 ? 4 : 8;
+  if (!d || !x) return set_error(TDP_EINVAL, std::string(fn) + ": null pointer");
+  if ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(x)) % el)
+    return set_error(TDP_EINVAL, std::string(fn) + ": pointer not aligned to its element");
+  if (d == x) return set_error(TDP_EINVAL, std::string(fn) + ": x must not alias d");
+  const int ss2 = s ? s : std::min(512, int(predict_s(n, batch, dtype)));
+  return run(stream, fn, [&](Ctx& ctx) {
+    solve_const(ctx, a, b, c, d, x, n, batch, sys_stride, elem_stride, ss2, dtype, refine_iters);
+  });
+}
+
 int tdp_solve_strided(int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
                       const void* b, const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype,
                       int32_t refine_iters, void* stream) {

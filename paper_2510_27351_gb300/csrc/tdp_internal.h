@@ -68,6 +68,8 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
                   int s, tdp_dtype dt, int refine_iters);
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
                    const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
+void solve_const(Ctx& ctx, double a, double b, double c, const void* d, void* x, int64_t n, int32_t batch,
+                 int64_t ss, int64_t es, int s, tdp_dtype dt, int refine_iters);
 void predict_sizes(Ctx& ctx, const int64_t* offsets, int32_t batch, tdp_dtype dt, int32_t* s_out);
 void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t sys_stride, int64_t elem_stride, const void* a,
                    const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);

@@ -17,6 +17,7 @@
 #include "tdp_coop.cuh"
 #include "tdp_wtile.cuh"
 #include "tdp_refine.cuh"
+#include "tdp_const.cuh"
 
 namespace tdp {
 
@@ -1010,6 +1011,84 @@ BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
 // ---------------------------------------------------------------------------
 // Public drivers
 // ---------------------------------------------------------------------------
+namespace {
+// One constant-coefficient solve: table, Stage 1, interface, Stage 3.
+template <typename S, typename C>
+void const_pass(Ctx& ctx, double a, double b, double c, const S* d, S* x, int64_t n, int32_t batch, int64_t ss,
+                int64_t es, int s) {
+  const int64_t mps = (n + s - 1) / s;
+  const int64_t m = int64_t(batch) * mps;
+  C* tab = ctx.ar->take<C>(6 * size_t(s));
+  double* ra = ctx.ar->take<double>(2 * m);
+  double* rb = ctx.ar->take<double>(2 * m);
+  double* rc = ctx.ar->take<double>(2 * m);
+  double* rd = ctx.ar->take<double>(2 * m);
+  double* y = ctx.ar->take<double>(2 * m);
+  int T = 128;
+  while (T > 32 && size_t(T) * s * sizeof(C) > size_t(kMaxSmem)) T -= 32;
+  const size_t smem = size_t(T) * s * sizeof(C);
+  const unsigned grid = unsigned((m + T - 1) / T);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    if (smem > size_t(kMaxSmem)) {
+      ctx.fail(cudaErrorInvalidConfiguration, "constant-coefficient tile");
+      return;
+    }
+    pre_launch(ctx, "const_table");
+    k_const_table<C><<<1, 32, 0, ctx.stream>>>(a, b, c, s, tab, ctx.status);
+    post_launch(ctx, "constant-coefficient table");
+    auto k1 = k_const_stage1<S, C>;
+    allow_smem(k1);
+    pre_launch(ctx, sizeof(C) == 8 ? "const_stage1_f64" : "const_stage1_f32");
+    k1<<<grid, T, smem, ctx.stream>>>(a, b, c, tab, d, n, batch, s, mps, ss, es, ra, rb, rc, rd, ctx.status);
+    post_launch(ctx, "constant-coefficient stage 1");
+  }
+  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    auto k3 = k_const_stage3<S, C>;
+    allow_smem(k3);
+    pre_launch(ctx, sizeof(C) == 8 ? "const_stage3_f64" : "const_stage3_f32");
+    k3<<<grid, T, smem, ctx.stream>>>(tab, d, x, n, batch, s, mps, ss, es, y);
+    post_launch(ctx, "constant-coefficient stage 3");
+  }
+}
+}  // namespace
+
+void solve_const(Ctx& ctx, double a, double b, double c, const void* d, void* x, int64_t n, int32_t batch,
+                 int64_t ss, int64_t es, int s, tdp_dtype dt, int refine_iters) {
+  ctx.rec_n = int64_t(batch) * n;
+  ctx.rec_batch = batch;
+  ctx.rec_dt = dt;
+  if (batch <= 0 || n <= 0) return;
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  if (dt == TDP_F64) {
+    const_pass<double, double>(ctx, a, b, c, (const double*)d, (double*)x, n, batch, ss, es, s);
+  } else if (dt == TDP_F32) {
+    const_pass<float, float>(ctx, a, b, c, (const float*)d, (float*)x, n, batch, ss, es, s);
+  } else {
+    // binary32 solves on binary64 storage, binary64 residual and update
+    const double* D = (const double*)d;
+    double* X = (double*)x;
+    const int64_t span = int64_t(batch - 1) * ss + (n - 1) * es + 1;
+    double* r = ctx.ar->take<double>(refine_iters > 0 ? span : 1);
+    double* dx = ctx.ar->take<double>(refine_iters > 0 ? span : 1);
+    const_pass<double, float>(ctx, a, b, c, D, X, n, batch, ss, es, s);
+    const int64_t total = int64_t(batch) * n;
+    for (int it = 0; it < refine_iters; ++it) {
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "const_residual_f64");
+        k_const_residual<<<grid_for(total, 256), 256, 0, ctx.stream>>>(a, b, c, D, X, r, n, batch, ss, es);
+        post_launch(ctx, "constant-coefficient residual");
+      }
+      const_pass<double, float>(ctx, a, b, c, r, dx, n, batch, ss, es, s);
+      if (!ctx.dry && ctx.err == cudaSuccess) {
+        pre_launch(ctx, "const_update_f64");
+        k_const_update<<<grid_for(total, 256), 256, 0, ctx.stream>>>(X, dx, n, batch, ss, es);
+        post_launch(ctx, "constant-coefficient update");
+      }
+    }
+  }
+}
+
 int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap) {
   if (R < 0) R = int(predict_r(n, batch, dt));
   int64_t M = 2 * ((n + s - 1) / s);

@@ -47,6 +47,15 @@ def test_bad_arguments_rejected_on_host():
     # batched: batch < 1, null offsets
     assert lib.tdp_solve_batched(16, 0, 10, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
     assert lib.tdp_solve_batched(0, 1, 10, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
+    # constant coefficients: s too large, zero stride, overlapping systems, aliasing, misaligned
+    f = lib.tdp_solve_const
+    assert f(-1.0, 4.0, -1.0, 16, 32, 10, 2, 10, 1, 600, 0, 0, 0) == 1
+    assert f(-1.0, 4.0, -1.0, 16, 32, 10, 2, 0, 1, 4, 0, 0, 0) == 1
+    assert f(-1.0, 4.0, -1.0, 16, 32, 10, 2, 5, 1, 4, 0, 0, 0) == 1
+    assert "overlap" in tdp.tdp_last_error()
+    assert f(-1.0, 4.0, -1.0, 16, 16, 10, 2, 10, 1, 4, 0, 0, 0) == 1
+    assert f(-1.0, 4.0, -1.0, 20, 32, 10, 2, 10, 1, 4, 0, 0, 0) == 1
+    assert "aligned" in tdp.tdp_last_error()
     # strided: bad strides
     assert lib.tdp_solve_strided(2, 8, -1, 1, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
     # backward refuses the refinement dtype

@@ -363,3 +363,55 @@ def test_paper_recursion_schedule(tdp, code):
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_RECURSION, old[0])
         tdp.tdp_set_tuning(tdp.TUNE_R, old[1])
+
+
+def _const_ref(a, b, c, d2, n, batch, ss, es):
+    """Oracle Thomas on materialised constant diagonals for the strided layout."""
+    size = int((batch - 1) * ss + (n - 1) * es + 1)
+    A, B, C = np.full(size, a), np.full(size, b), np.full(size, c)
+    base = np.arange(batch, dtype=np.int64) * ss
+    return oracle.thomas_batched(A, B, C, d2, base=base, length=np.full(batch, n), elem_stride=es)
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_constant_coefficients_vs_oracle(tdp, code):
+    """tdp_solve_const against Thomas on the materialised diagonals: one system,
+    back-to-back systems and interleaved systems (the column sweep layout),
+    sizes with a ragged last block, every s from 2 to 512."""
+    import torch
+
+    dt = torch.float32 if code == 1 else torch.float64
+    a, b, c = -0.45, 2.1, -0.55
+    for n, batch, layout in ((1, 1, "seq"), (2, 3, "seq"), (3, 2, "int"), (5, 7, "int"), (64, 1, "seq"),
+                             (1000, 5, "seq"), (4099, 33, "int"), (100_003, 2, "seq")):
+        ss, es = (n, 1) if layout == "seq" else (1, batch)
+        size = (batch - 1) * ss + (n - 1) * es + 1
+        d2 = W.uniform(n + batch, 5, size, -1, 1)
+        ref = _const_ref(a, b, c, d2, n, batch, ss, es)
+        D = dev(d2, dt)
+        for s in (2, 3, 4, 8, 16, 32, 64, 100, 512, 0):
+            x = torch.zeros_like(D)
+            tdp.tdp_solve_const(a, b, c, D, x, n, batch, ss, es, s, code, 1 if code == 2 else 0)
+            torch.cuda.synchronize()
+            e = oracle.rel_err(host(x), ref)
+            assert e <= TOL[code], (n, batch, layout, s, e)
+
+
+def test_constant_heat_step_closed_form(tdp):
+    """The implicit heat step (b = 1 + 2r, a = c = -r) along rows then columns
+    against the sine-basis closed form of tridiag(-r, 1+2r, -r)."""
+    import torch
+
+    n, r = 512, 0.5
+    H = W.heat(n, r, seed=2)
+    u = H.u.reshape(-1)
+    rows_ref = np.concatenate([oracle.dst_const(n, r, u[i * n:(i + 1) * n]) for i in range(n)])
+    cols_ref = np.stack([oracle.dst_const(n, r, rows_ref.reshape(n, n)[:, j]) for j in range(n)], axis=1).reshape(-1)
+    U = dev(u)
+    rows = torch.empty_like(U)
+    tdp.tdp_solve_const(-r, 1 + 2 * r, -r, U, rows, n, n, n, 1, 0, 2, 1)
+    cols = torch.empty_like(U)
+    tdp.tdp_solve_const(-r, 1 + 2 * r, -r, rows, cols, n, n, 1, n, 0, 2, 1)
+    torch.cuda.synchronize()
+    assert oracle.rel_err(host(rows), rows_ref) <= 1e-12
+    assert oracle.rel_err(host(cols), cols_ref) <= 1e-12
