@@ -64,6 +64,71 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned* status) {
   return __syncthreads_and(ok) != 0;
 }
 
+// Parallel cyclic reduction of a system of M <= 64 rows by one warp (the
+// last interface system): lane l holds rows l and l + 32; every step h =
+// 1, 2, .., 32 eliminates the couplings to rows i - h and i + h (neighbour
+// rows read with shuffles), after which x_i = d_i / b_i.  Rows beyond M are
+// identity rows.  All 32 lanes must call it.
+__device__ __forceinline__ void warp_pcr64(const double* a, const double* b, const double* c, const double* d,
+                                           double* y, int M, unsigned* status) {
+  const int l = threadIdx.x & 31;
+  double A[2], B[2], C[2], Dv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = l + 32 * h;
+    const bool in = i < M;
+    A[h] = (in && i > 0) ? a[i] : 0.0;
+    B[h] = in ? b[i] : 1.0;
+    C[h] = (in && i < M - 1) ? c[i] : 0.0;
+    Dv[h] = in ? d[i] : 0.0;
+  }
+#pragma unroll
+  for (int hs = 1; hs <= 32; hs <<= 1) {
+    const int up = (l - hs) & 31, dn = (l + hs) & 31;
+    double ua[2], ub[2], uc[2], ud[2], wa[2], wb[2], wc[2], wd[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      ua[h] = __shfl_sync(0xffffffffu, A[h], up); ub[h] = __shfl_sync(0xffffffffu, B[h], up);
+      uc[h] = __shfl_sync(0xffffffffu, C[h], up); ud[h] = __shfl_sync(0xffffffffu, Dv[h], up);
+      wa[h] = __shfl_sync(0xffffffffu, A[h], dn); wb[h] = __shfl_sync(0xffffffffu, B[h], dn);
+      wc[h] = __shfl_sync(0xffffffffu, C[h], dn); wd[h] = __shfl_sync(0xffffffffu, Dv[h], dn);
+    }
+    double nA[2], nB[2], nC[2], nD[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // row i = l + 32 h; its upper neighbour i - hs and lower neighbour i + hs
+      const int i = l + 32 * h;
+      const int iu = i - hs, iw = i + hs;
+      const int hu = (iu >= 0) ? (iu >> 5) : 0, hw = (iw < 64) ? (iw >> 5) : 0;
+      const bool vu = iu >= 0, vw = iw < 64;
+      const double Au = hu ? ua[1] : ua[0], Bu = hu ? ub[1] : ub[0], Cu = hu ? uc[1] : uc[0],
+                   Du = hu ? ud[1] : ud[0];
+      const double Aw = hw ? wa[1] : wa[0], Bw = hw ? wb[1] : wb[0], Cw = hw ? wc[1] : wc[0],
+                   Dw = hw ? wd[1] : wd[0];
+      const double k1 = vu ? A[h] * rcp(Bu, status) : 0.0;
+      const double k2 = vw ? C[h] * rcp(Bw, status) : 0.0;
+      nA[h] = vu ? -k1 * Au : 0.0;
+      nC[h] = vw ? -k2 * Cw : 0.0;
+      nB[h] = B[h] - (vu ? k1 * Cu : 0.0) - (vw ? k2 * Aw : 0.0);
+      nD[h] = Dv[h] - (vu ? k1 * Du : 0.0) - (vw ? k2 * Dw : 0.0);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) { A[h] = nA[h]; B[h] = nB[h]; C[h] = nC[h]; Dv[h] = nD[h]; }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = l + 32 * h;
+    if (i < M) y[i] = Dv[h] * rcp(B[h], status);
+  }
+}
+
+// A system of at most 64 rows solved by one warp (launch with 32 threads).
+__global__ void __launch_bounds__(32) k_base_pcr(const double* __restrict__ a, const double* __restrict__ b,
+                                                 const double* __restrict__ c, const double* __restrict__ d,
+                                                 double* __restrict__ y, int M, unsigned* __restrict__ status) {
+  warp_pcr64(a, b, c, d, y, M, status);
+}
+
 // Stage 1 of one block read from global memory; forward values go to the
 // kept arrays and are replaced by the primes of the backward pass.
 __device__ __forceinline__ void coop_block_reduce(const CoopLevel& D, int64_t k, unsigned* status) {
@@ -139,8 +204,11 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
     for (int64_t k = tid; k < D.m; k += nth) coop_block_reduce(D, k, status);
     ok = grid_barrier(bar, status);
   }
-  if (ok && tid == 0) {
-    // Thomas on the last system (2m rows of the deepest level)
+  if (ok && blockIdx.x == 0 && threadIdx.x < 32 && 2 * P.lv[P.L - 1].m <= 64) {
+    const CoopLevel& D = P.lv[P.L - 1];
+    warp_pcr64(D.na, D.nb, D.nc, D.nd, P.ybase, int(2 * D.m), status);
+  } else if (ok && tid == 0) {
+    // Thomas on the last system (2m rows of the deepest level) when it is larger
     const CoopLevel& D = P.lv[P.L - 1];
     const int64_t M = 2 * D.m;
     double gam = 0.0, del = 0.0;

@@ -482,11 +482,9 @@ void solve_interface_rec(Ctx& ctx, const double* ra, const double* rb, const dou
   const int s2 = (level <= R && M > kBaseRows) ? paper_level_size(level, R, M) : 0;
   if (s2 == 0 || s2 >= M) {
     if (M <= kBaseRows) {
-      double* scratch = ctx.ar->take<double>(M);
       if (ctx.dry || ctx.err != cudaSuccess) return;
       pre_launch(ctx, "interface_base");
-      k_thomas<double, double><<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, nullptr, 1, M, 0, 1, M, scratch,
-                                                          ctx.status);
+      k_base_pcr<<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, int(M), ctx.status);
       post_launch(ctx, "interface base solve");
     } else {
       solve_interface_coop(ctx, ra, rb, rc, rd, y, M);
@@ -521,11 +519,9 @@ void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double*
     return;
   }
   if (M <= kBaseRows) {
-    double* scratch = ctx.ar->take<double>(M);
     if (ctx.dry || ctx.err != cudaSuccess) return;
     pre_launch(ctx, "interface_base");
-    k_thomas<double, double><<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, nullptr, 1, M, 0, 1, M, scratch,
-                                                        ctx.status);
+    k_base_pcr<<<1, 32, 0, ctx.stream>>>(ra, rb, rc, rd, y, int(M), ctx.status);
     post_launch(ctx, "interface base solve");
     return;
   }
