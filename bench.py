@@ -469,19 +469,21 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
     ms = cuda_time(heat, steps, 2, stream)
     out["heat_2048"] = {"ms": ms, "unknowns_per_s": 2 * 2048 * 2048 / (ms * 1e-3), "dtype": "fp32_refine1"}
 
-    # the same step through the constant-coefficient path (d in, x out)
-    def heat_const():
-        tdp.tdp_solve_const(-0.5, 2.0, -0.5, hd["u"], r1, 2048, 2048, 2048, 1, 0, tdp.F32_REFINE, 1, stream)
-        tdp.tdp_solve_const(-0.5, 2.0, -0.5, r1, r2, 2048, 2048, 1, 2048, 0, tdp.F32_REFINE, 1, stream)
+    # the same step through the constant-coefficient path (d in, x out), with s
+    # from the constant-path autotuner
+    from paper_2510_27351_gb300 import tune
 
-    ms = cuda_time(heat_const, steps, 2, stream)
-    out["heat_2048_const"] = {"ms": ms, "unknowns_per_s": 2 * 2048 * 2048 / (ms * 1e-3), "dtype": "fp32_refine1",
-                              "kernels_ms": {k: v[1] for k, v in profile_kernels(tdp, heat_const, 3).items()}}
-    for name, code, it in (("heat_2048_const_f64", tdp.F64, 0),):
-        fn = lambda: (tdp.tdp_solve_const(-0.5, 2.0, -0.5, hd["u"], r1, 2048, 2048, 2048, 1, 0, code, it, stream),
-                      tdp.tdp_solve_const(-0.5, 2.0, -0.5, r1, r2, 2048, 2048, 1, 2048, 0, code, it, stream))
+    for name, code, it in (("heat_2048_const", tdp.F32_REFINE, 1), ("heat_2048_const_f64", tdp.F64, 0)):
+        def step(s, code=code, it=it):
+            tdp.tdp_solve_const(-0.5, 2.0, -0.5, hd["u"], r1, 2048, 2048, 2048, 1, s, code, it, stream)
+            tdp.tdp_solve_const(-0.5, 2.0, -0.5, r1, r2, 2048, 2048, 1, 2048, s, code, it, stream)
+
+        s_best, _ = tune.autotune_const(step)
+        fn = lambda: step(s_best)
         ms = cuda_time(fn, steps, 2, stream)
-        out[name] = {"ms": ms, "unknowns_per_s": 2 * 2048 * 2048 / (ms * 1e-3), "dtype": "f64"}
+        out[name] = {"ms": ms, "unknowns_per_s": 2 * 2048 * 2048 / (ms * 1e-3), "s": s_best,
+                     "dtype": "fp32_refine1" if code == tdp.F32_REFINE else "f64",
+                     "kernels_ms": {k: v[1] for k, v in profile_kernels(tdp, fn, 3).items()}}
     return out
 
 

@@ -210,6 +210,8 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_RECURSION 10   /* 1: the interface system follows the paper's recursion schedule (Sec. III);
                                    0: s = TDP_TUNE_S_REC levels down to 2^19 rows, then the one-launch tail */
 #define TDP_TUNE_R 11           /* number of recursive steps of that schedule, -1 = tdp_predict_r [-1, 12] */
+#define TDP_TUNE_SEGMENTED 12   /* 1: batches of >= 32 systems with at most 512 interface rows per system on
+                                   average solve them one CTA per system */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

@@ -241,3 +241,95 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
 }
 
 }  // namespace tdp
+
+namespace tdp {
+
+// ---------------------------------------------------------------------------
+// Segmented interface solve: the interface system of a batch is the
+// concatenation of one decoupled interface system per system (a system's
+// first interface row has no coupling to the left, its last none to the
+// right).  One CTA solves one system's rows with the same method, on chip:
+//   level 1: the rows in P <= blockDim.x blocks of q rows, one per thread
+//            (rows read from L2, kept coefficients to global scratch),
+//   level 2: the 2P interface rows in shared memory, reduced by warp 0 in
+//            blocks of at most 16 rows to <= 64 rows,
+//   base:    warp parallel cyclic reduction of those rows,
+//   then Stage 3 of level 2 (warp 0) and of level 1 (every thread).
+// No grid-wide synchronisation.  The rows of system j are
+// [rows(j), rows(j+1)) with rows(j) = 2 bbase[j] (bbase: blocks before
+// system j) or, when bbase is null, 2 j per_sys.
+// ---------------------------------------------------------------------------
+constexpr int kSegT = 256;         // threads per CTA (level-1 blocks at most)
+constexpr int kSegM2 = 2 * kSegT;  // level-2 rows at most
+
+struct __align__(16) SegSmem {
+  double a2[kSegM2], b2[kSegM2], c2[kSegM2], d2[kSegM2];  // level-2 system
+  double ka2[kSegM2], kg2[kSegM2], kd2[kSegM2];            // its kept coefficients
+  double y2[kSegM2];                                       // its solution
+  double a3[64], b3[64], c3[64], d3[64], y3[64];          // level-3 system and solution
+};
+
+__global__ void __launch_bounds__(kSegT) k_iface_seg(const double* __restrict__ ra, const double* __restrict__ rb,
+                                                     const double* __restrict__ rc, const double* __restrict__ rd,
+                                                     double* __restrict__ y, const int64_t* __restrict__ bbase,
+                                                     int64_t per_sys, int32_t batch, double* __restrict__ ka,
+                                                     double* __restrict__ kg, double* __restrict__ kd,
+                                                     unsigned* __restrict__ status) {
+  __shared__ SegSmem sm;
+  for (int64_t j = blockIdx.x; j < batch; j += gridDim.x) {
+    const int64_t R0 = bbase ? 2 * bbase[j] : 2 * j * per_sys;
+    const int64_t R1 = bbase ? 2 * bbase[j + 1] : 2 * (j + 1) * per_sys;
+    const int64_t M = R1 - R0;
+    const int t = threadIdx.x, lane = t & 31;
+    if (M <= 0) continue;  // uniform across the CTA
+    if (M <= 64) {
+      if (t < 32) warp_pcr64(ra + R0, rb + R0, rc + R0, rd + R0, y + R0, int(M), status);
+      __syncthreads();
+      continue;
+    }
+    // level 1
+    const int64_t q = (M + 2 * kSegT - 1) / (2 * kSegT) * 2;  // even, P = ceil(M / q) <= kSegT blocks
+    const int P = int((M + q - 1) / q);
+    CoopLevel D1;
+    D1.a = ra + R0; D1.b = rb + R0; D1.c = rc + R0; D1.d = rd + R0;
+    D1.ka = ka + R0; D1.kg = kg + R0; D1.kd = kd + R0;
+    D1.na = sm.a2; D1.nb = sm.b2; D1.nc = sm.c2; D1.nd = sm.d2;
+    D1.y = nullptr;
+    D1.M = M; D1.m = P; D1.s = int(q);
+    if (t < P) coop_block_reduce(D1, t, status);
+    __syncthreads();
+    // level 2 (warp 0), the base system and Stage 3 of level 2
+    const int M2 = 2 * P;
+    if (t < 32) {
+      if (M2 <= 64) {
+        warp_pcr64(sm.a2, sm.b2, sm.c2, sm.d2, sm.y2, M2, status);
+      } else {
+        const int q2 = (M2 + 31) / 32;  // <= 16
+        const int P2 = (M2 + q2 - 1) / q2;
+        CoopLevel D2;
+        D2.a = sm.a2; D2.b = sm.b2; D2.c = sm.c2; D2.d = sm.d2;
+        D2.ka = sm.ka2; D2.kg = sm.kg2; D2.kd = sm.kd2;
+        D2.na = sm.a3; D2.nb = sm.b3; D2.nc = sm.c3; D2.nd = sm.d3;
+        D2.y = nullptr;
+        D2.M = M2; D2.m = P2; D2.s = q2;
+        if (lane < P2) coop_block_reduce(D2, lane, status);
+        __syncwarp();
+        warp_pcr64(sm.a3, sm.b3, sm.c3, sm.d3, sm.y3, 2 * P2, status);
+        __syncwarp();
+        for (int i = lane; i < M2; i += 32) {
+          const int k = i / q2;
+          sm.y2[i] = fma(-sm.kg2[i], sm.y3[2 * k + 1], fma(-sm.ka2[i], sm.y3[2 * k], sm.kd2[i]));
+        }
+      }
+    }
+    __syncthreads();
+    // Stage 3 of level 1
+    for (int64_t i = t; i < M; i += kSegT) {
+      const int64_t k = i / q;
+      y[R0 + i] = fma(-kg[R0 + i], sm.y2[2 * k + 1], fma(-ka[R0 + i], sm.y2[2 * k], kd[R0 + i]));
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tdp

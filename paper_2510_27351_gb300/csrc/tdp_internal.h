@@ -43,6 +43,10 @@ struct Ctx {
   int64_t rec_n = 1;           // size, batch and dtype the recursion depth is predicted for
   int32_t rec_batch = 1;
   tdp_dtype rec_dt = TDP_F64;
+  bool seg = true;                   // per-system interface solves for batches (TDP_SEGMENTED=0 off)
+  const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
+  int64_t seg_per = 0;                 // before each system (device), or blocks per system
+  int32_t seg_batch = 0;
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)

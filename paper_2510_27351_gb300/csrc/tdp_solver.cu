@@ -506,8 +506,34 @@ void solve_interface_rec(Ctx& ctx, const double* ra, const double* rb, const dou
   stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f64");
 }
 
+void solve_interface_levels(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
+                            double* y, int64_t M);
+
+// One CTA per system when the interface system is a batch's concatenation of
+// small decoupled systems (k_iface_seg).
+bool solve_interface_seg(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
+                         int64_t M) {
+  if (!ctx.seg || ctx.seg_batch < 32 || M / ctx.seg_batch > 512 || ctx.rec_mode == 1) return false;
+  double* ka = ctx.ar->take<double>(M);
+  double* kg = ctx.ar->take<double>(M);
+  double* kd = ctx.ar->take<double>(M);
+  if (ctx.dry || ctx.err != cudaSuccess) return true;
+  pre_launch(ctx, "iface_seg");
+  k_iface_seg<<<unsigned(std::min<int64_t>(ctx.seg_batch, 1 << 20)), kSegT, 0, ctx.stream>>>(
+      ra, rb, rc, rd, y, ctx.seg_bbase, ctx.seg_per, ctx.seg_batch, ka, kg, kd, ctx.status);
+  post_launch(ctx, "segmented interface solve");
+  return true;
+}
+
 void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
                      int64_t M) {
+  if (M <= 0) return;
+  if (solve_interface_seg(ctx, ra, rb, rc, rd, y, M)) return;
+  solve_interface_levels(ctx, ra, rb, rc, rd, y, M);
+}
+
+void solve_interface_levels(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
+                            double* y, int64_t M) {
   if (M <= 0) return;
   if (ctx.rec_mode == 1) {
     const int R = ctx.rec_force >= 0 ? ctx.rec_force : int(predict_r(ctx.rec_n, ctx.rec_batch, ctx.rec_dt));
@@ -537,7 +563,7 @@ void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double*
   double* y2 = ctx.ar->take<double>(2 * m2);
   stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd,
                                       "iface_stage1_f64");
-  solve_interface(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
+  solve_interface_levels(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
   stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f64");
 }
 
@@ -932,9 +958,26 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
   }
 }
 
+// While alive, the interface solves of ctx belong to a batch of `batch`
+// systems (blocks before each in bbase, or per_sys blocks each).
+struct SegScope {
+  Ctx& c;
+  SegScope(Ctx& ctx, const int64_t* bbase, int64_t per_sys, int32_t batch) : c(ctx) {
+    c.seg_bbase = bbase;
+    c.seg_per = per_sys;
+    c.seg_batch = batch;
+  }
+  ~SegScope() {
+    c.seg_bbase = nullptr;
+    c.seg_per = 0;
+    c.seg_batch = 0;
+  }
+};
+
 struct BatchMap {
   const int64_t* blk = nullptr;
   const uint8_t* edge = nullptr;
+  const int64_t* bbase = nullptr;  // blocks before each system
   int64_t m = 0;
 };
 
@@ -979,6 +1022,7 @@ BatchMap build_map(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
   int32_t* sj = model ? ctx.ar->take<int32_t>(batch) : nullptr;
   bm.blk = blk;
   bm.edge = edge;
+  bm.bbase = bbase;
   if (ctx.dry || ctx.err != cudaSuccess) return bm;
   if (model) {
     pre_launch(ctx, "predict_sizes");
@@ -1020,6 +1064,7 @@ void const_pass(Ctx& ctx, double a, double b, double c, const S* d, S* x, int64_
   double* rc = ctx.ar->take<double>(2 * m);
   double* rd = ctx.ar->take<double>(2 * m);
   double* y = ctx.ar->take<double>(2 * m);
+  SegScope seg(ctx, nullptr, mps, batch);
   int T = 128;
   while (T > 32 && size_t(T) * s * sizeof(C) > size_t(kMaxSmem)) T -= 32;
   const size_t smem = size_t(T) * s * sizeof(C);
@@ -1120,12 +1165,14 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
     static thread_local SizeModel model;
     if (size_model(dt, batch, &model)) {
       BatchMap bm = build_map(ctx, offsets, batch, total_n, model.s_max, edges, &model);
+      SegScope seg(ctx, bm.bbase, 0, batch);
       solve_blocks<true>(ctx, a, b, c, d, x, total_n, model.s_max, bm.m, bm.blk, bm.edge, dt, refine_iters);
       return;
     }
     s = predict_s((total_n + batch - 1) / batch, batch, dt);
   }
   BatchMap bm = build_map(ctx, offsets, batch, total_n, s, edges);
+  SegScope seg(ctx, bm.bbase, 0, batch);
   solve_blocks<true>(ctx, a, b, c, d, x, total_n, s, bm.m, bm.blk, bm.edge, dt, refine_iters);
 }
 

@@ -317,6 +317,18 @@ def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(
                     torch.cuda.empty_cache()
 
 
+def autotune_const(fn, s_grid=(8, 16, 32, 64, 128), reps=10):
+    """Fastest s for a constant-coefficient solve: ``fn(s)`` queues the solve(s)
+    with sub-system size s on the current stream; every s of the grid is timed
+    (CUDA events) after one untimed call.  Returns (s, ms)."""
+    best = None
+    for s in s_grid:
+        ms = _time_ms(lambda: fn(s), reps)
+        if best is None or ms < best[1]:
+            best = (s, ms)
+    return best
+
+
 # ---------------------------------------------------------------------------
 # number of recursive steps (Sec. III)
 # ---------------------------------------------------------------------------

@@ -415,3 +415,30 @@ def test_constant_heat_step_closed_form(tdp):
     torch.cuda.synchronize()
     assert oracle.rel_err(host(rows), rows_ref) <= 1e-12
     assert oracle.rel_err(host(cols), cols_ref) <= 1e-12
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_segmented_interface_solve(tdp, code):
+    """Batches of >= 32 systems solve their interface systems one CTA per
+    system (TDP_TUNE_SEGMENTED): interface systems from a few rows (warp
+    cyclic reduction only) to tens of thousands (two levels on chip), empty
+    and one-row systems; the same answer with the knob on and off."""
+    import torch
+
+    sizes = [0, 1, 2, 3, 40, 100, 1000, 5000, 20000, 65536] * 4
+    Sb = W.batched(sizes=sizes, seed=21)
+    ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+    dt = torch.float32 if code == 1 else torch.float64
+    a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+    off = dev(Sb.offsets)
+    old = tdp.tdp_get_tuning(tdp.TUNE_SEGMENTED)
+    try:
+        for seg in (1, 0):
+            tdp.tdp_set_tuning(tdp.TUNE_SEGMENTED, seg)
+            for s in (4, 16, 0):
+                x = torch.full_like(d, float("nan"))
+                tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, s, code, 1 if code == 2 else 0)
+                torch.cuda.synchronize()
+                assert oracle.rel_err(host(x), ref) <= TOL[code], (seg, s)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_SEGMENTED, old)
