@@ -64,20 +64,19 @@ __device__ __forceinline__ double widen(float f) {
 }
 
 // binary64 -> binary32 with integer operations (the hardware conversion also
-// runs on the binary64 pipe).  The top 32 bits of the 64-bit pattern shifted
-// left by 3 hold the low 9 exponent bits and the top 23 mantissa bits; adding
-// 128 to the exponent field (mod 512) rebiases every exponent of the binary32
-// normal range, and the first dropped mantissa bit rounds to nearest (ties
-// away from zero; a carry into the exponent is the correct next binade).
-// Magnitudes below the binary32 normal range give signed zero, above it
-// infinity; nan stays nan.
+// runs on the binary64 pipe), rounding toward zero.  The top 32 bits of the
+// 64-bit pattern shifted left by 3 hold the low 9 exponent bits and the top 23
+// mantissa bits; adding 128 to the exponent field (mod 512) rebiases every
+// exponent of the binary32 normal range.  Magnitudes below that range give
+// signed zero, above it (and nan) infinity.  Used for the inputs of the
+// binary32 solves inside the binary64 refinement, whose result the binary64
+// residual corrects.
 __device__ __forceinline__ float narrow(double v) {
   const unsigned hi = unsigned(__double2hiint(v)), lo = unsigned(__double2loint(v));
   const unsigned mag = hi & 0x7fffffffu;
-  unsigned w = (__funnelshift_l(lo, hi, 3) + (128u << 23) + ((lo >> 28) & 1u)) & 0x7fffffffu;
-  if (mag < (897u << 20)) w = 0u;
-  if (mag >= (1151u << 20)) w = (mag > 0x7ff00000u || (mag == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
-  return __uint_as_float(w | (hi & 0x80000000u));
+  unsigned w = __funnelshift_l(lo, hi, 3) + (128u << 23);
+  w = mag < (897u << 20) ? 0u : (mag >= (1151u << 20) ? 0x7f800000u : w);
+  return __uint_as_float((w & 0x7fffffffu) | (hi & 0x80000000u));
 }
 
 template <typename C> __device__ __forceinline__ C cvt(double v);
