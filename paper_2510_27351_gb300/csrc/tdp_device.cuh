@@ -174,4 +174,26 @@ __device__ __forceinline__ int64_t block_start(int64_t k, int64_t n, int s, cons
   }
 }
 
+// 16-byte shared-memory vector load and store.
+template <typename S>
+__device__ __forceinline__ Vec<S> lds16(const S* p) {
+  Vec<S> r;
+  if constexpr (sizeof(S) == 8) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  }
+  return r;
+}
+template <typename S>
+__device__ __forceinline__ void sts16(S* p, const Vec<S>& r) {
+  if constexpr (sizeof(S) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  }
+}
+
 }  // namespace tdp

@@ -10,7 +10,7 @@
 // consecutive 16-byte words).  ldv = T + 1 spreads the copies of one warp over
 // all banks.
 #pragma once
-#include "tdp_kernels.cuh"
+#include "tdp_lean.cuh"
 
 namespace tdp {
 
@@ -20,27 +20,6 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_commit_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-template <typename S>
-__device__ __forceinline__ Vec<S> lds16(const S* p) {
-  Vec<S> r;
-  if constexpr (sizeof(S) == 8) {
-    const double2 t = *reinterpret_cast<const double2*>(p);
-    r.v[0] = t.x; r.v[1] = t.y;
-  } else {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  }
-  return r;
-}
-template <typename S>
-__device__ __forceinline__ void sts16(S* p, const Vec<S>& r) {
-  if constexpr (sizeof(S) == 8) {
-    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
-  } else {
-    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-  }
 }
 
 // Tile rows [ts, te) of NA arrays into the interleaved layout.  Chunks that
@@ -266,7 +245,20 @@ __global__ void __launch_bounds__(256) k_stage1_v(const S* __restrict__ a, const
   __syncthreads();
   if (t < nb) {
     const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
-    const IfaceRows r = vblock_reduce<S, C, KEEP>(pl[0], pl[1], pl[2], pl[3], ldv, t, bi, status);
+    IfaceRows r;
+    if constexpr (std::is_same<C, float>::value && !KEEP) {
+      if (bi.len == s) {
+        constexpr int V = Vec<S>::W;
+        float z = 0.0f;
+        r = wreduce_full<S>(pl[0] + t * V, pl[1] + t * V, pl[2] + t * V, pl[3] + t * V, s, ldv * V, bi.first,
+                            bi.last, z);
+        if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+      } else {
+        r = vblock_reduce<S, C, KEEP>(pl[0], pl[1], pl[2], pl[3], ldv, t, bi, status);
+      }
+    } else {
+      r = vblock_reduce<S, C, KEEP>(pl[0], pl[1], pl[2], pl[3], ldv, t, bi, status);
+    }
     write_iface(k0 + t, r, ra, rb, rc, rd);
   }
   if constexpr (KEEP) {
@@ -297,7 +289,18 @@ __global__ void __launch_bounds__(256) k_stage3_resolve_v(const S* __restrict__ 
   if (t < nb) {
     const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
     const double2 v = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));
-    vblock_substitute<S, C>(pl[0], pl[1], pl[2], pl[3], ldv, t, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
+    bool lean = false;
+    if constexpr (std::is_same<C, float>::value) {
+      if (bi.len == s) {
+        constexpr int V = Vec<S>::W;
+        float z = 0.0f;
+        wsubstitute_full<S>(pl[0] + t * V, pl[1] + t * V, pl[2] + t * V, pl[3] + t * V, s, ldv * V, v.x, v.y, z);
+        if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+        lean = true;
+      }
+    }
+    if (!lean)
+      vblock_substitute<S, C>(pl[0], pl[1], pl[2], pl[3], ldv, t, bi.len, cvt<C>(v.x), cvt<C>(v.y), status);
   }
   __syncthreads();
   const S* const from[1] = {pl[3]};
