@@ -432,7 +432,7 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
         ms_graph = cuda_time(g.replay, steps, 2, torch.cuda.current_stream())  # replay() launches there
         res[name] = {"ms": ms, "ms_graph": ms_graph, "unknowns_per_s": Sb.n / (ms * 1e-3),
                      "unknowns_per_s_graph": Sb.n / (ms_graph * 1e-3), "hbm_frac_40B": hbm(ms, 40 * Sb.n),
-                     "s": "per system (device 1-NN)", "rel_err_vs_xstar": err}
+                     "s": tdp.tdp_predict_s(Sb.n // Sb.batch, Sb.batch, code), "rel_err_vs_xstar": err}
         del g
     fn = lambda: tdp.tdp_thomas_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx,
                                         tdp.F64, stream)

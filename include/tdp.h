@@ -75,10 +75,12 @@ int tdp_solve(const void* a, const void* b, const void* c, const void* d, void* 
  *  total_n    : offsets[batch] (passed by value so that no copy to the host is
  *               needed; the device checks it and reports TDP_EINVAL through
  *               the status word when it disagrees).
- *  s          : sub-system size for every system (2..1024), or 0 to choose
- *               one per system on the device with the size model
- *               (tdp_predict_s_batched), capped at the largest size the
- *               model gives for the nearest batch size in its table.
+ *  s          : sub-system size for every system (2..1024), or 0 for the
+ *               size model's choice for the mean system size and the batch
+ *               size (tdp_predict_s); with the tuning key
+ *               TDP_TUNE_PER_SYSTEM_S = 1, s = 0 instead gives every system
+ *               its own size on the device (tdp_predict_s_batched), capped at
+ *               the largest size the model gives for the nearest batch size.
  * Empty systems are allowed.  Other arguments as tdp_solve. */
 int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                       const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
@@ -212,6 +214,7 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_R 11           /* number of recursive steps of that schedule, -1 = tdp_predict_r [-1, 12] */
 #define TDP_TUNE_SEGMENTED 12   /* 1: batches of >= 32 systems with at most 512 interface rows per system on
                                    average solve them one CTA per system */
+#define TDP_TUNE_PER_SYSTEM_S 13 /* 1: tdp_solve_batched with s = 0 gives every system its own s (device model) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

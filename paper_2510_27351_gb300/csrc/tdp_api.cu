@@ -74,21 +74,22 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // refinement passes, the TMA-staged tiles, the element-copy warp-tile
 // pipeline, the warp-owned bulk-copy tiles and the three-pass refinement),
 // TDP_RECURSION (1: the paper's recursion schedule), TDP_R (its number of
-// recursive steps, -1 = predicted) and TDP_SEGMENTED (1: one CTA per system
-// for the interface systems of batches).
+// recursive steps, -1 = predicted), TDP_SEGMENTED (1: one CTA per system
+// for the interface systems of batches) and TDP_PER_SYSTEM_S (1: batched
+// solves with s = 0 choose s per system on the device).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[13] = {
+Knob g_knobs[14] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
     {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
     {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
     {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
     {"TDP_RECURSION", 0, 1, {0}},                          {"TDP_R", -1, 12, {-1}},
-    {"TDP_SEGMENTED", 0, 1, {1}},
+    {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
 };
 std::once_flag g_knobs_once;
 
@@ -118,6 +119,7 @@ void tune_from_env(Ctx& ctx) {
   ctx.rec_mode = g_knobs[TDP_TUNE_RECURSION].v.load();
   ctx.rec_force = g_knobs[TDP_TUNE_R].v.load();
   ctx.seg = g_knobs[TDP_TUNE_SEGMENTED].v.load() != 0;
+  ctx.per_system_s = g_knobs[TDP_TUNE_PER_SYSTEM_S].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

@@ -44,6 +44,7 @@ struct Ctx {
   int32_t rec_batch = 1;
   tdp_dtype rec_dt = TDP_F64;
   bool seg = true;                   // per-system interface solves for batches (TDP_SEGMENTED=0 off)
+  bool per_system_s = false;         // batched s = 0: one s per system from the device model (TDP_PER_SYSTEM_S=1)
   const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
   int64_t seg_per = 0;                 // before each system (device), or blocks per system
   int32_t seg_batch = 0;

@@ -1161,9 +1161,11 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
   if (batch <= 0 || total_n <= 0) return;
   const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;
   if (s == 0) {
-    // per-system sizes from the device predictor; tiles sized for the largest
+    // per-system sizes from the device predictor (TDP_PER_SYSTEM_S=1); the
+    // tiles are sized for the largest of them, so by default one s for the
+    // batch's mean system size is used instead
     static thread_local SizeModel model;
-    if (size_model(dt, batch, &model)) {
+    if (ctx.per_system_s && size_model(dt, batch, &model)) {
       BatchMap bm = build_map(ctx, offsets, batch, total_n, model.s_max, edges, &model);
       SegScope seg(ctx, bm.bbase, 0, batch);
       solve_blocks<true>(ctx, a, b, c, d, x, total_n, model.s_max, bm.m, bm.blk, bm.edge, dt, refine_iters);

@@ -273,6 +273,8 @@ def test_batched_per_system_sizes(tdp, tmp_path):
     p = tmp_path / "t.txt"
     p.write_text("0 64 4096 4\n0 2000 4096 8\n0 20000 4096 32\n2 64 4096 8\n2 50000 4096 16\n")
     tdp.tdp_load_table(str(p))
+    old = tdp.tdp_get_tuning(tdp.TUNE_PER_SYSTEM_S)
+    tdp.tdp_set_tuning(tdp.TUNE_PER_SYSTEM_S, 1)
     try:
         Sb = W.batched(512, 64, 65536, seed=11)
         ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
@@ -284,6 +286,7 @@ def test_batched_per_system_sizes(tdp, tmp_path):
             torch.cuda.synchronize()
             assert oracle.rel_err(host(x), ref) <= 1e-12, code
     finally:
+        tdp.tdp_set_tuning(tdp.TUNE_PER_SYSTEM_S, old)
         tdp.tdp_load_table("")
 
 
