@@ -19,6 +19,11 @@ the rule it implements.
 * ``split_3to1`` / ``grid_search_k`` / ``accuracy`` / ``null_accuracy``:
   the evaluation protocol of Sec. II-E (shuffled 3:1 split keeping every
   class in training, k searched in [1, #classes] by cross-validation).
+* ``interval_rule_r``: the number of recursive steps R read off the paper's
+  table of optimum R (Sec. III-A); ``knn_predict`` serves its 1-NN model too.
+* ``recursive_sizes``: the sub-system sizes of the R recursive steps
+  (Sec. III-B): the first step 10 when R >= 2, every other step the size
+  model applied to the interface system that step partitions.
 """
 from __future__ import annotations
 
@@ -147,6 +152,35 @@ def correct_labels(times, tol: float = 0.05):
         raise RuntimeError("no non-decreasing label sequence within tolerance")
     final = min(best[0].values(), key=lambda v: v[:3])
     return raw, list(final[3])[::-1]
+
+
+def interval_rule_r(n: float, table) -> int:
+    """table = [(N_upper, R), ...] ascending; returns R for N, the last R + 1
+    above the last bound (Sec. III-A)."""
+    for upper, r in table:
+        if n <= upper:
+            return int(r)
+    return int(table[-1][1]) + 1
+
+
+def recursive_sizes(n: int, s: int, R: int, predict_s, base_rows: int = 64):
+    """Sub-system sizes m_1..m_R of the recursive steps for one system of n
+    unknowns partitioned with s (Sec. III-B).  The interface system of a
+    partition into ceil(M/m) blocks has 2 ceil(M/m) rows.  Steps stop early
+    once the interface system has at most ``base_rows`` rows or the step
+    would form a single block (nothing left to reduce)."""
+    sizes = []
+    M = 2 * math.ceil(n / s)
+    for level in range(1, R + 1):
+        if M <= base_rows:
+            break
+        m = 10 if (level == 1 and R >= 2) else int(predict_s(M))
+        m = max(m, 3)
+        if m >= M:
+            break
+        sizes.append(m)
+        M = 2 * math.ceil(M / m)
+    return sizes
 
 
 def load_table(path):
