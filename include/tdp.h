@@ -215,6 +215,11 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_SEGMENTED 12   /* 1: batches of >= 32 systems with at most 512 interface rows per system on
                                    average solve them one CTA per system */
 #define TDP_TUNE_PER_SYSTEM_S 13 /* 1: tdp_solve_batched with s = 0 gives every system its own s (device model) */
+#define TDP_TUNE_IFACE32 14     /* 1: TDP_F32 and TDP_F32_REFINE solve the first level of their interface
+                                   recursion (interface systems above 2^19 rows) in binary32 arithmetic:
+                                   their Stage 3 reads the interface values as binary32 anyway */
+#define TDP_TUNE_REFINE_KEPT 15 /* 1: the refinement's second pass keeps the correction's Stage-1 coefficients
+                                   (binary32) so that its last pass is elementwise (104 instead of 120 B/row) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

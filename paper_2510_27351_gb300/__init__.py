@@ -81,7 +81,8 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
- TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S) = range(14)
+ TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S,
+ TUNE_IFACE32, TUNE_REFINE_KEPT) = range(16)
 
 
 def _check(rc: int):

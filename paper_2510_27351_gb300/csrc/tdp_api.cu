@@ -75,14 +75,17 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // pipeline, the warp-owned bulk-copy tiles and the three-pass refinement),
 // TDP_RECURSION (1: the paper's recursion schedule), TDP_R (its number of
 // recursive steps, -1 = predicted), TDP_SEGMENTED (1: one CTA per system
-// for the interface systems of batches) and TDP_PER_SYSTEM_S (1: batched
-// solves with s = 0 choose s per system on the device).
+// for the interface systems of batches), TDP_PER_SYSTEM_S (1: batched
+// solves with s = 0 choose s per system on the device), TDP_IFACE32 (1:
+// the first level of the interface recursion of binary32 solves in binary32
+// arithmetic) and TDP_REFINE_KEPT (1: the last refinement pass elementwise
+// from kept binary32 coefficients).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[14] = {
+Knob g_knobs[16] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
     {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
@@ -90,6 +93,7 @@ Knob g_knobs[14] = {
     {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
     {"TDP_RECURSION", 0, 1, {0}},                          {"TDP_R", -1, 12, {-1}},
     {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
+    {"TDP_IFACE32", 0, 1, {1}},                            {"TDP_REFINE_KEPT", 0, 1, {1}},
 };
 std::once_flag g_knobs_once;
 
@@ -120,6 +124,8 @@ void tune_from_env(Ctx& ctx) {
   ctx.rec_force = g_knobs[TDP_TUNE_R].v.load();
   ctx.seg = g_knobs[TDP_TUNE_SEGMENTED].v.load() != 0;
   ctx.per_system_s = g_knobs[TDP_TUNE_PER_SYSTEM_S].v.load() != 0;
+  ctx.iface32 = g_knobs[TDP_TUNE_IFACE32].v.load() != 0;
+  ctx.refine_kept = g_knobs[TDP_TUNE_REFINE_KEPT].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

@@ -45,6 +45,9 @@ struct Ctx {
   tdp_dtype rec_dt = TDP_F64;
   bool seg = true;                   // per-system interface solves for batches (TDP_SEGMENTED=0 off)
   bool per_system_s = false;         // batched s = 0: one s per system from the device model (TDP_PER_SYSTEM_S=1)
+  bool iface32 = true;               // binary32 arithmetic in the first interface level of binary32 solves (TDP_IFACE32)
+  bool iface32_on = false;           // set while such a solve runs
+  bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
   const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
   int64_t seg_per = 0;                 // before each system (device), or blocks per system
   int32_t seg_batch = 0;

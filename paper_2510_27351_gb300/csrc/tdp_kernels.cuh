@@ -369,6 +369,13 @@ __global__ void __launch_bounds__(256) k_stage3_kept(const C* __restrict__ ka, c
 #pragma unroll
       for (int e = 0; e < V; ++e) vx.v[e] = cvt<S>(xv[e]);
       stg16<S>(x + base, vx);
+    } else if (full && sizeof(S) == 2 * sizeof(C)) {  // binary32 chunk -> two binary64 chunks
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int e = 0; e < Vec<S>::W; ++e) vx.v[e] = cvt<S>(xv[h * Vec<S>::W + e]);
+        stg16<S>(x + base + h * Vec<S>::W, vx);
+      }
     } else {
 #pragma unroll
       for (int e = 0; e < V; ++e) {

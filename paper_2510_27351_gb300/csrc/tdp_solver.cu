@@ -283,16 +283,18 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       }
     }
   }
-  if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
-    size_t smem;
-    const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
-    auto vk = k_stage1_v<S, C, KEEP>;
-    allow_smem(vk);
-    pre_launch(ctx, nm);
-    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
-                                                           ctx.status);
-    post_launch(ctx, "stage 1");
-    return;
+  if constexpr (!MAPPED && std::is_same<S, C>::value) {
+    if (ctx.vtile && s % Vec<S>::W == 0) {
+      size_t smem;
+      const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
+      auto vk = k_stage1_v<S, C, KEEP>;
+      allow_smem(vk);
+      pre_launch(ctx, nm);
+      vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
+                                                             ctx.status);
+      post_launch(ctx, "stage 1");
+      return;
+    }
   }
   if (ctx.tma) {
     auto tk = k_stage1_tma<S, C, MAPPED, KEEP>;
@@ -553,19 +555,44 @@ void solve_interface_levels(Ctx& ctx, const double* ra, const double* rb, const 
   }
   const int s2 = ctx.s_rec;
   const int64_t m2 = (M + s2 - 1) / s2;
-  double* ka = ctx.ar->take<double>(M);
-  double* kg = ctx.ar->take<double>(M);
-  double* kd = ctx.ar->take<double>(M);
   double* ra2 = ctx.ar->take<double>(2 * m2);
   double* rb2 = ctx.ar->take<double>(2 * m2);
   double* rc2 = ctx.ar->take<double>(2 * m2);
   double* rd2 = ctx.ar->take<double>(2 * m2);
   double* y2 = ctx.ar->take<double>(2 * m2);
+  if (ctx.iface32_on) {
+    // A binary32 solve reads its interface values as binary32: the first
+    // level (the largest by a factor s_rec) runs in binary32 arithmetic on
+    // the binary64 rows, the deeper levels in binary64.  (Sending the next
+    // interface system straight to the one-launch tail with a larger s was
+    // slower: that tail's cost grows with its first level's size.)
+    float* ka = ctx.ar->take<float>(M);
+    float* kg = ctx.ar->take<float>(M);
+    float* kd = ctx.ar->take<float>(M);
+    stage1<double, float, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd,
+                                       "iface_stage1_f32");
+    ctx.iface32_on = false;
+    solve_interface_levels(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
+    ctx.iface32_on = true;
+    stage3_kept<float, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f32");
+    return;
+  }
+  double* ka = ctx.ar->take<double>(M);
+  double* kg = ctx.ar->take<double>(M);
+  double* kd = ctx.ar->take<double>(M);
   stage1<double, double, false, true>(ctx, ra, rb, rc, rd, M, s2, m2, nullptr, ra2, rb2, rc2, rd2, ka, kg, kd,
                                       "iface_stage1_f64");
   solve_interface_levels(ctx, ra2, rb2, rc2, rd2, y2, 2 * m2);
   stage3_kept<double, double, false>(ctx, ka, kg, kd, M, s2, m2, nullptr, y2, y, "iface_stage3_f64");
 }
+
+// While alive, the interface solves of ctx belong to a binary32 solve.
+struct Iface32Scope {
+  Ctx& c;
+  bool old;
+  Iface32Scope(Ctx& ctx, bool on) : c(ctx), old(ctx.iface32_on) { c.iface32_on = on && ctx.iface32; }
+  ~Iface32Scope() { c.iface32_on = old; }
+};
 
 // ---------------------------------------------------------------------------
 // Helper kernels: block map, residual, update, transposition, gradients.
@@ -858,6 +885,7 @@ bool refine_fused(Ctx& ctx, const void* a, const void* b, const void* c, const v
 template <bool MAPPED>
 void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
                   int64_t m, const int64_t* blk, const uint8_t* edge, tdp_dtype dt, int refine_iters) {
+  Iface32Scope f32(ctx, dt != TDP_F64);
   double* ra = ctx.ar->take<double>(2 * m);
   double* rb = ctx.ar->take<double>(2 * m);
   double* rc = ctx.ar->take<double>(2 * m);
@@ -886,7 +914,12 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
     // separate kernels for any further correction
     const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
     double* X = (double*)x;
-    float* rr = ctx.ar->take<float>(n);
+    const bool kept = ctx.refine_kept;
+    float* rr = ctx.ar->take<float>(kept ? 1 : n);
+    float* x0f = kept ? ctx.ar->take<float>(n) : nullptr;
+    float* fka = kept ? ctx.ar->take<float>(n) : nullptr;
+    float* fkg = kept ? ctx.ar->take<float>(n) : nullptr;
+    float* fkd = kept ? ctx.ar->take<float>(n) : nullptr;
     double* r = ctx.ar->take<double>(refine_iters > 1 ? n : 1);
     double* dx = ctx.ar->take<double>(refine_iters > 1 ? n : 1);
     stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
@@ -895,15 +928,24 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
     if (!ctx.dry && ctx.err == cudaSuccess) {
       size_t smem;
       const int T = pick_threads(ctx, s, 5, 4, MAPPED, &smem);
-      auto kern = k_refine_mid<MAPPED>;
+      auto kern = kept ? k_refine_mid<MAPPED, true> : k_refine_mid<MAPPED, false>;
       allow_smem(kern);
       pre_launch(ctx, "refine_mid");
       kern<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(A, B, Cc, D, X, rr, n, s, magic_for(s), m, blk, edge,
-                                                               y, ra, rb, rc, rd, ctx.status);
+                                                               y, ra, rb, rc, rd, x0f, fka, fkg, fkd, ctx.status);
       post_launch(ctx, "refine pass 2");
     }
     solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
-    if (!ctx.dry && ctx.err == cudaSuccess) {
+    if (!ctx.dry && ctx.err == cudaSuccess && kept) {
+      size_t smem;
+      const int T = pick_threads(ctx, s, 4, 4, MAPPED, &smem);
+      const size_t need = size_t(2) * T * sizeof(float) + (MAPPED ? size_t(4) * T * s : 0);
+      auto kern = k_refine_kept<MAPPED>;
+      allow_smem(kern);
+      pre_launch(ctx, "refine_kept");
+      kern<<<unsigned((m + T - 1) / T), T, need, ctx.stream>>>(fka, fkg, fkd, x0f, n, s, magic_for(s), m, blk, y, X);
+      post_launch(ctx, "refine pass 3");
+    } else if (!ctx.dry && ctx.err == cudaSuccess) {
       size_t smem;
       const int T = pick_threads(ctx, s, 4, 4, MAPPED, &smem);
       auto kern = k_refine_last<MAPPED>;
@@ -1100,6 +1142,7 @@ void solve_const(Ctx& ctx, double a, double b, double c, const void* d, void* x,
   ctx.rec_batch = batch;
   ctx.rec_dt = dt;
   if (batch <= 0 || n <= 0) return;
+  Iface32Scope f32(ctx, dt != TDP_F64);
   if (s > n) s = int(std::max<int64_t>(2, n));
   if (dt == TDP_F64) {
     const_pass<double, double>(ctx, a, b, c, (const double*)d, (double*)x, n, batch, ss, es, s);

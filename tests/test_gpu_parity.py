@@ -445,3 +445,36 @@ def test_segmented_interface_solve(tdp, code):
                 assert oracle.rel_err(host(x), ref) <= TOL[code], (seg, s)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_SEGMENTED, old)
+
+
+@pytest.mark.parametrize("kept", [0, 1])
+def test_refinement_last_pass_variants(tdp, kept):
+    """Both forms of the refinement's last pass (re-solve from a, b, c and the
+    binary32 residual, or elementwise from the kept binary32 coefficients),
+    single systems with ragged last blocks and a batch with empty, one-row
+    and two-row systems."""
+    import torch
+
+    old = tdp.tdp_get_tuning(tdp.TUNE_REFINE_KEPT)
+    tdp.tdp_set_tuning(tdp.TUNE_REFINE_KEPT, kept)
+    try:
+        for n in (1, 2, 3, 5, 33, 1000, 4097, 100_003):
+            S = W.single(n, seed=100 + n)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for s in (2, 3, 8, 24, 32, 100):
+                for iters in (1, 2):
+                    e = oracle.rel_err(_solve(tdp, S, s, 2, iters), ref)
+                    assert e <= TOL[2], (kept, n, s, iters, e)
+        sizes = [0, 1, 2, 3, 5, 64, 65, 127, 1000, 0, 4097, 31, 32, 33, 1]
+        Sb = W.batched(sizes=sizes, seed=5)
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        a, b, c, d = (dev(v) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+        off = dev(Sb.offsets)
+        for s in (2, 4, 24, 100):
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(off, len(sizes), Sb.n, a, b, c, d, x, s, 2, 1)
+            torch.cuda.synchronize()
+            e = oracle.rel_err(host(x), ref)
+            assert e <= TOL[2], (kept, s, e)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_REFINE_KEPT, old)
