@@ -123,6 +123,9 @@ int tdp_solve_strided(int32_t batch, int64_t n, int64_t sys_stride, int64_t elem
  *  grad_*     : device arrays of total_n elements; any may be NULL to skip it
  *               (grad_d is lambda and is computed even when NULL is passed
  *               for it, into workspace).
+ * The transposed diagonals are written with zeros at every system boundary,
+ * so the whole batch is solved as one system of total_n rows; s (0 = the size
+ * model for one system of total_n rows) partitions that system.
  * dtype TDP_F64 or TDP_F32. */
 int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                        const void* c, const void* x, const void* g, void* grad_a, void* grad_b, void* grad_c,
@@ -220,6 +223,7 @@ int64_t tdp_launch_count(void);
                                    their Stage 3 reads the interface values as binary32 anyway */
 #define TDP_TUNE_REFINE_KEPT 15 /* 1: the refinement's second pass keeps the correction's Stage-1 coefficients
                                    (binary32) so that its last pass is elementwise (104 instead of 120 B/row) */
+#define TDP_TUNE_COOP_REG 16    /* 1: the one-launch interface tail reads its 8-row blocks into registers */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

@@ -78,14 +78,15 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // for the interface systems of batches), TDP_PER_SYSTEM_S (1: batched
 // solves with s = 0 choose s per system on the device), TDP_IFACE32 (1:
 // the first level of the interface recursion of binary32 solves in binary32
-// arithmetic) and TDP_REFINE_KEPT (1: the last refinement pass elementwise
-// from kept binary32 coefficients).
+// arithmetic), TDP_REFINE_KEPT (1: the last refinement pass elementwise
+// from kept binary32 coefficients) and TDP_COOP_REG (1: the one-launch tail
+// reads full 8-row blocks into registers).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[16] = {
+Knob g_knobs[17] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
     {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
@@ -94,6 +95,7 @@ Knob g_knobs[16] = {
     {"TDP_RECURSION", 0, 1, {0}},                          {"TDP_R", -1, 12, {-1}},
     {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
     {"TDP_IFACE32", 0, 1, {1}},                            {"TDP_REFINE_KEPT", 0, 1, {1}},
+    {"TDP_COOP_REG", 0, 1, {1}},
 };
 std::once_flag g_knobs_once;
 
@@ -126,6 +128,7 @@ void tune_from_env(Ctx& ctx) {
   ctx.per_system_s = g_knobs[TDP_TUNE_PER_SYSTEM_S].v.load() != 0;
   ctx.iface32 = g_knobs[TDP_TUNE_IFACE32].v.load() != 0;
   ctx.refine_kept = g_knobs[TDP_TUNE_REFINE_KEPT].v.load() != 0;
+  ctx.coop_reg = g_knobs[TDP_TUNE_COOP_REG].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.
@@ -526,7 +529,8 @@ int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, c
   if ((rc = check_ptrs({a, b, c, x, g}, "tdp_solve_backward"))) return rc;
   for (const void* p : {(const void*)grad_a, (const void*)grad_b, (const void*)grad_c, (const void*)grad_d})
     if (p && !aligned16(p)) return set_error(TDP_EINVAL, "tdp_solve_backward: gradient not 16-byte aligned");
-  const int ss = s ? s : predict_s((total_n + batch - 1) / batch, batch, dtype);
+  // the transposed batch is solved as one system of total_n rows
+  const int ss = s ? s : predict_s(total_n, 1, dtype);
   return run(stream, "tdp_solve_backward", [&](Ctx& ctx) {
     solve_backward(ctx, offsets, batch, total_n, a, b, c, x, g, grad_a, grad_b, grad_c, grad_d, ss, dtype);
   });

@@ -32,6 +32,7 @@ struct CoopLevel {
 struct CoopParams {
   CoopLevel lv[kCoopMaxLevels];
   int L;                 // number of levels
+  int reg;               // 1: blocks of 8 rows through registers (coop_block_reduce_reg)
   double* base_scratch;  // Thomas scratch for the last system
   double* ybase;         // solution of the last system (2 * lv[L-1].m rows)
 };
@@ -194,6 +195,105 @@ __device__ __forceinline__ void coop_block_reduce(const CoopLevel& D, int64_t k,
   *reinterpret_cast<double2*>(D.nd + 2 * k) = make_double2(r0d, r1d);
 }
 
+// The same for a block of 3 <= len <= S rows held in registers: every load is
+// issued before the first use (one L2 round trip per block instead of one
+// per row), the backward pass reads the forward values from registers, and a
+// full block's kept coefficients leave as 16-byte stores.  Loops run over all
+// S rows with the rows past len masked, so that a ragged last block takes the
+// same code path as its warp's full blocks.  The level's arrays must be
+// 16-byte aligned (arena buffers are).
+template <int S>
+__device__ __forceinline__ void coop_block_reduce_reg(const CoopLevel& D, int64_t k, int len, unsigned* status) {
+  static_assert(S >= 4 && S % 2 == 0, "even block size of at least 4");
+  const int64_t L = k * S;
+  const bool first = (k == 0), last = (k == D.m - 1), full = (len == S);
+  double a[S], b[S], c[S], d[S];
+  if (full) {
+#pragma unroll
+    for (int j = 0; j < S; j += 2) {
+      const double2 va = *reinterpret_cast<const double2*>(D.a + L + j);
+      const double2 vb = *reinterpret_cast<const double2*>(D.b + L + j);
+      const double2 vc = *reinterpret_cast<const double2*>(D.c + L + j);
+      const double2 vd = *reinterpret_cast<const double2*>(D.d + L + j);
+      a[j] = va.x; a[j + 1] = va.y; b[j] = vb.x; b[j + 1] = vb.y;
+      c[j] = vc.x; c[j + 1] = vc.y; d[j] = vd.x; d[j + 1] = vd.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const bool in = j < len;
+      a[j] = in ? D.a[L + j] : 0.0; b[j] = in ? D.b[L + j] : 1.0;
+      c[j] = in ? D.c[L + j] : 0.0; d[j] = in ? D.d[L + j] : 0.0;
+    }
+  }
+  if (first) a[0] = 0.0;
+  // forward: rows 1..len-1, (alpha, gamma, delta) replace (a, c, d).  (Row
+  // selections by len are written as per-row conditions inside the unrolled
+  // loops: a separate "element len-1" access would become a dynamically
+  // indexed array in local memory.)
+  double gam, del, alp;
+  {
+    const double r = rcp(b[1], status);
+    gam = c[1] * r; del = d[1] * r; alp = a[1] * r;
+    a[1] = alp; c[1] = gam; d[1] = del;
+  }
+  // the backward pass starts from row len-2's forward values
+  double ap = alp, gp = gam, dp = del;
+#pragma unroll
+  for (int j = 2; j < S; ++j) {
+    if (j < len) {
+      const double cj = (last && j == len - 1) ? 0.0 : c[j];
+      const double r = rcp(fma(-a[j], gam, b[j]), status);
+      const double q = a[j] * r;
+      gam = cj * r;
+      del = fma(-q, del, d[j] * r);
+      alp = -q * alp;
+      a[j] = alp; c[j] = gam; d[j] = del;
+      if (j == len - 2) { ap = alp; gp = gam; dp = del; }
+    }
+  }
+  const double r1a = alp, r1c = gam, r1d = del;
+  // backward over the interior rows len-3 .. 1
+#pragma unroll
+  for (int j = S - 3; j >= 1; --j) {
+    if (j < len - 2) {
+      const double gj = c[j];
+      dp = fma(-gj, dp, d[j]);
+      ap = fma(-gj, ap, a[j]);
+      gp = -gj * gp;
+      a[j] = ap; c[j] = gp; d[j] = dp;
+    }
+  }
+  const double r0a = a[0], r0b = fma(-c[0], ap, b[0]), r0c = -c[0] * gp, r0d = fma(-c[0], dp, d[0]);
+  // kept rows 0 and len-1 give x_L and x_R themselves
+  a[0] = -1.0; c[0] = 0.0; d[0] = 0.0;
+  if (full) {
+    a[S - 1] = 0.0; c[S - 1] = -1.0; d[S - 1] = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; j += 2) {
+      *reinterpret_cast<double2*>(D.ka + L + j) = make_double2(a[j], a[j + 1]);
+      *reinterpret_cast<double2*>(D.kg + L + j) = make_double2(c[j], c[j + 1]);
+      *reinterpret_cast<double2*>(D.kd + L + j) = make_double2(d[j], d[j + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j < len) {
+        const bool end = j == len - 1;
+        D.ka[L + j] = end ? 0.0 : a[j];
+        D.kg[L + j] = end ? -1.0 : c[j];
+        D.kd[L + j] = end ? 0.0 : d[j];
+      }
+    }
+  }
+  *reinterpret_cast<double2*>(D.na + 2 * k) = make_double2(r0a, r1a);
+  *reinterpret_cast<double2*>(D.nb + 2 * k) = make_double2(r0b, 1.0);
+  *reinterpret_cast<double2*>(D.nc + 2 * k) = make_double2(r0c, r1c);
+  *reinterpret_cast<double2*>(D.nd + 2 * k) = make_double2(r0d, r1d);
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ CoopParams P, unsigned* bar,
                                                     unsigned* status) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -201,7 +301,15 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
   bool ok = true;
   for (int l = 0; l < P.L && ok; ++l) {
     const CoopLevel& D = P.lv[l];
-    for (int64_t k = tid; k < D.m; k += nth) coop_block_reduce(D, k, status);
+    const bool reg8 = P.reg && D.s == 8 && aligned16(D.a) && aligned16(D.b) && aligned16(D.c) && aligned16(D.d) &&
+                      aligned16(D.ka) && aligned16(D.kg) && aligned16(D.kd);
+    for (int64_t k = tid; k < D.m; k += nth) {
+      const int len = int(min(int64_t(8), D.M - k * 8));
+      if (reg8 && len >= 3)
+        coop_block_reduce_reg<8>(D, k, len, status);
+      else
+        coop_block_reduce(D, k, status);
+    }
     ok = grid_barrier(bar, status);
   }
   if (ok && blockIdx.x == 0 && threadIdx.x < 32 && 2 * P.lv[P.L - 1].m <= 64) {

@@ -48,6 +48,7 @@ struct Ctx {
   bool iface32 = true;               // binary32 arithmetic in the first interface level of binary32 solves (TDP_IFACE32)
   bool iface32_on = false;           // set while such a solve runs
   bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
+  bool coop_reg = true;              // one-launch tail: 8-row blocks through registers (TDP_COOP_REG)
   const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
   int64_t seg_per = 0;                 // before each system (device), or blocks per system
   int32_t seg_batch = 0;

@@ -437,6 +437,7 @@ void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const do
     if (Ml > kBaseRows && L < kCoopMaxLevels) yl = ctx.ar->take<double>(Ml);
   }
   P.L = L;
+  P.reg = ctx.coop_reg ? 1 : 0;
   P.base_scratch = ctx.ar->take<double>(Ml);
   P.ybase = (L > 0) ? ctx.ar->take<double>(Ml) : y;
   unsigned* bar = ctx.ar->take<unsigned>(2);
@@ -1308,7 +1309,10 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
                                                                          (float*)aT, (float*)cT, total_n, edge);
     post_launch(ctx, "transpose");
   }
-  solve_batched(ctx, offsets, batch, total_n, aT, b, cT, g, lam, s, dt, 0);
+  // The transposed diagonals carry explicit zeros at every system boundary,
+  // so the batch is one block-diagonal tridiagonal system of total_n rows:
+  // it takes the single-system path (no block map; 16-byte tiles).
+  solve_single(ctx, aT, b, cT, g, lam, total_n, s, dt, 0);
   if (!ctx.dry && ctx.err == cudaSuccess && (ga || gb || gc)) {
     pre_launch(ctx, "gradients");
     if (el == 8)

@@ -478,3 +478,24 @@ def test_refinement_last_pass_variants(tdp, kept):
             assert e <= TOL[2], (kept, s, e)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_REFINE_KEPT, old)
+
+
+@pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 0)])
+def test_tuning_variants(tdp, key, value):
+    """Non-default kernel choices give the same answers: register-staged
+    tiles instead of the interleaved cp.async tiles, the one-launch tail
+    without register-resident blocks, every interface level in binary64.
+    Sizes reach the interface levels above 2^19 rows."""
+    k = getattr(tdp, key)
+    old = tdp.tdp_get_tuning(k)
+    tdp.tdp_set_tuning(k, value)
+    try:
+        for n in (1000, 100_003, 1 << 20, 1 << 22):
+            S = W.single(n, seed=7 + n)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for code in (0, 1, 2):
+                for s in (8, 24, 32):
+                    e = oracle.rel_err(_solve(tdp, S, s, code), ref)
+                    assert e <= TOL[code], (key, value, n, code, s, e)
+    finally:
+        tdp.tdp_set_tuning(k, old)
