@@ -50,6 +50,18 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def batched_s(tdp, Sb, code):
+    """The sub-system size tdp_solve_batched(s=0) uses: batches of systems of
+    at least 4096 rows on average run as one block-diagonal system with the
+    single-system model's s (if that s suits the 16-byte tiles), others
+    with the model at the mean system size."""
+    if tdp.tdp_get_tuning(tdp.TUNE_BATCH_FLAT) and Sb.batch >= 2 and Sb.n >= 4096 * Sb.batch:
+        s1 = tdp.tdp_predict_s(Sb.n, 1, code)
+        if code == tdp.F32_REFINE or s1 % (2 if code == tdp.F64 else 4) == 0:
+            return s1
+    return tdp.tdp_predict_s(max(1, Sb.n // Sb.batch), Sb.batch, code)
+
+
 def measured_traffic(kernel, s, n):
     """DRAM bytes per launch of ``kernel`` from the committed ncu capture
     (profiles/traffic.json), scaled to n rows; None when the kernel sources
@@ -432,7 +444,7 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
         ms_graph = cuda_time(g.replay, steps, 2, torch.cuda.current_stream())  # replay() launches there
         res[name] = {"ms": ms, "ms_graph": ms_graph, "unknowns_per_s": Sb.n / (ms * 1e-3),
                      "unknowns_per_s_graph": Sb.n / (ms_graph * 1e-3), "hbm_frac_40B": hbm(ms, 40 * Sb.n),
-                     "s": tdp.tdp_predict_s(Sb.n // Sb.batch, Sb.batch, code), "rel_err_vs_xstar": err}
+                     "s": batched_s(tdp, Sb, code), "rel_err_vs_xstar": err}
         del g
     fn = lambda: tdp.tdp_thomas_batched(boff, Sb.batch, Sb.n, bdev["a"], bdev["b"], bdev["c"], bdev["d"], bx,
                                         tdp.F64, stream)

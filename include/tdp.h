@@ -224,6 +224,8 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_REFINE_KEPT 15 /* 1: the refinement's second pass keeps the correction's Stage-1 coefficients
                                    (binary32) so that its last pass is elementwise (104 instead of 120 B/row) */
 #define TDP_TUNE_COOP_REG 16    /* 1: the one-launch interface tail reads its 8-row blocks into registers */
+#define TDP_TUNE_BATCH_FLAT 17  /* 1: tdp_solve_batched with at least 4096 rows per system on average solves the
+                                   batch as one block-diagonal system on the single-system tiles */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

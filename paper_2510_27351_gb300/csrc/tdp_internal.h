@@ -49,6 +49,9 @@ struct Ctx {
   bool iface32_on = false;           // set while such a solve runs
   bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
   bool coop_reg = true;              // one-launch tail: 8-row blocks through registers (TDP_COOP_REG)
+  bool batch_flat = true;            // batches of large systems as one block-diagonal system (TDP_BATCH_FLAT)
+  const int64_t* flat_off = nullptr; // set while such a batch is solved: its offsets (device)
+  int32_t flat_nsys = 0;             // and number of systems
   const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
   int64_t seg_per = 0;                 // before each system (device), or blocks per system
   int32_t seg_batch = 0;

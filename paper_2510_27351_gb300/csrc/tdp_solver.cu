@@ -291,7 +291,7 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       allow_smem(vk);
       pre_launch(ctx, nm);
       vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
-                                                             ctx.status);
+                                                             ctx.flat_off, ctx.flat_nsys, ctx.status);
       post_launch(ctx, "stage 1");
       return;
     }
@@ -366,7 +366,8 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
     auto vk = k_stage3_resolve_v<S, C>;
     allow_smem(vk);
     pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
-    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.status);
+    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.flat_off, ctx.flat_nsys,
+                                                           ctx.status);
     post_launch(ctx, "stage 3");
     return;
   }
@@ -531,8 +532,14 @@ bool solve_interface_seg(Ctx& ctx, const double* ra, const double* rb, const dou
 void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
                      int64_t M) {
   if (M <= 0) return;
-  if (solve_interface_seg(ctx, ra, rb, rc, rd, y, M)) return;
-  solve_interface_levels(ctx, ra, rb, rc, rd, y, M);
+  // the interface system has no system boundaries to cut
+  const int64_t* flat_off = ctx.flat_off;
+  const int32_t flat_nsys = ctx.flat_nsys;
+  ctx.flat_off = nullptr;
+  ctx.flat_nsys = 0;
+  if (!solve_interface_seg(ctx, ra, rb, rc, rd, y, M)) solve_interface_levels(ctx, ra, rb, rc, rd, y, M);
+  ctx.flat_off = flat_off;
+  ctx.flat_nsys = flat_nsys;
 }
 
 void solve_interface_levels(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
@@ -1197,6 +1204,69 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
   solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
 }
 
+// While alive, the single-system kernels cut the couplings between the
+// systems of a batch inside their tiles (k_stage1_v, k_stage3_resolve_v).
+struct FlatScope {
+  Ctx& c;
+  FlatScope(Ctx& ctx, const int64_t* off, int32_t nsys) : c(ctx) {
+    c.flat_off = off;
+    c.flat_nsys = nsys;
+  }
+  ~FlatScope() {
+    c.flat_off = nullptr;
+    c.flat_nsys = 0;
+  }
+};
+
+// a2 = a, c2 = c with a of every system's first row and c of its last row
+// set to zero (the diagonals as one block-diagonal system).
+template <typename S>
+__global__ void k_cut_edges(const int64_t* __restrict__ off, int32_t batch, S* __restrict__ a2, S* __restrict__ c2) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < batch; j += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t lo = off[j], hi = off[j + 1];
+    if (hi > lo) {
+      a2[lo] = S(0);
+      c2[hi - 1] = S(0);
+    }
+  }
+}
+
+// Batches of large systems are solved as ONE system of total_n rows whose
+// couplings across system boundaries are zero (a block-diagonal tridiagonal
+// system): the single-system tiles (16-byte cp.async, no block map) then
+// serve batches too.  Blocks may straddle a boundary; elimination across a
+// zero coupling is exact.  Binary64 and binary32 cut the couplings inside the
+// interleaved tiles, which requires those tiles for every kernel that reads
+// a and c; the refinement (whose passes read a and c in several layouts)
+// works on copies of a and c with the couplings zeroed.
+bool flat_batch(const Ctx& ctx, int32_t batch, int64_t total_n, tdp_dtype dt, int s) {
+  if (!ctx.batch_flat || batch < 2 || total_n < int64_t(batch) * 4096) return false;
+  if (dt == TDP_F32_REFINE) return true;
+  const int V = dt == TDP_F64 ? 2 : 4;
+  return ctx.vtile && !ctx.wtile && s % V == 0;
+}
+
+void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
+                const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
+  if (s > total_n) s = int(std::max<int64_t>(2, total_n));
+  const int64_t m = (total_n + s - 1) / s;
+  if (dt != TDP_F32_REFINE) {
+    FlatScope fs(ctx, offsets, batch);
+    solve_blocks<false>(ctx, a, b, c, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);
+    return;
+  }
+  double* a2 = ctx.ar->take<double>(total_n);
+  double* c2 = ctx.ar->take<double>(total_n);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    ctx.fail(cudaMemcpyAsync(a2, a, size_t(total_n) * 8, cudaMemcpyDeviceToDevice, ctx.stream), "copy of a");
+    ctx.fail(cudaMemcpyAsync(c2, c, size_t(total_n) * 8, cudaMemcpyDeviceToDevice, ctx.stream), "copy of c");
+    pre_launch(ctx, "cut_edges");
+    k_cut_edges<double><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, a2, c2);
+    post_launch(ctx, "cut edges");
+  }
+  solve_blocks<false>(ctx, a2, b, c2, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);
+}
+
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                    const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
   ctx.rec_n = total_n;
@@ -1216,6 +1286,11 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
       return;
     }
     s = predict_s((total_n + batch - 1) / batch, batch, dt);
+    if (flat_batch(ctx, batch, total_n, dt, predict_s(total_n, 1, dt))) s = predict_s(total_n, 1, dt);
+  }
+  if (flat_batch(ctx, batch, total_n, dt, s)) {
+    solve_flat(ctx, offsets, batch, total_n, a, b, c, d, x, s, dt, refine_iters);
+    return;
   }
   BatchMap bm = build_map(ctx, offsets, batch, total_n, s, edges);
   SegScope seg(ctx, bm.bbase, 0, batch);

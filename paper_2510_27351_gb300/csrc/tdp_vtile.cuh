@@ -24,10 +24,11 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 
 // Tile rows [ts, te) of NA arrays into the interleaved layout.  Chunks that
 // reach past the end of an array (n not a multiple of V) are read element by
-// element.
+// element.  vtile_issue starts the copies, cp_async_commit_wait_all waits
+// for them (vtile_load does both).
 template <typename S, int NA>
-__device__ __forceinline__ void vtile_load(int64_t ts, int64_t te, int64_t n, int s, int ldv,
-                                           const S* const (&src)[NA], S* const (&pl)[NA]) {
+__device__ __forceinline__ void vtile_issue(int64_t ts, int64_t te, int64_t n, int s, int ldv,
+                                            const S* const (&src)[NA], S* const (&pl)[NA]) {
   constexpr int V = Vec<S>::W;
   const int chunks = int((te - ts + V - 1) / V);
   const int cps = s / V;  // chunks per block
@@ -45,7 +46,56 @@ __device__ __forceinline__ void vtile_load(int64_t ts, int64_t te, int64_t n, in
         for (int u = 0; u < V; ++u) pl[i][idx + u] = (row + u < n) ? src[i][row + u] : S(0);
     }
   }
+}
+
+template <typename S, int NA>
+__device__ __forceinline__ void vtile_load(int64_t ts, int64_t te, int64_t n, int s, int ldv,
+                                           const S* const (&src)[NA], S* const (&pl)[NA]) {
+  vtile_issue<S, NA>(ts, te, n, s, ldv, src, pl);
   cp_async_commit_wait_all();
+}
+
+// Smallest j in [lo, hi) with off[j] >= key (hi if none), off non-decreasing;
+// all 32 lanes of a warp call it.  Each round probes 32 evenly spaced entries
+// at once, so a batch of B systems takes about log32(B) dependent loads.
+__device__ __forceinline__ int warp_lower_bound(const int64_t* off, int lo, int hi, int64_t key) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int j = lo + lane * step;
+    const bool ge = (j >= hi) || off[j] >= key;
+    const unsigned msk = __ballot_sync(0xffffffffu, ge);
+    const int f = msk ? __ffs(msk) - 1 : 32;
+    if (f == 0) return lo;
+    // probe f-1 is below key, probe f (if any) at or above it
+    const int nlo = lo + (f - 1) * step + 1;
+    hi = min(hi, lo + f * step);
+    lo = nlo;
+  }
+  const int j = lo + lane;
+  const bool ge = (j >= hi) || off[j] >= key;
+  const unsigned msk = __ballot_sync(0xffffffffu, ge);
+  return msk ? lo + __ffs(msk) - 1 : hi;
+}
+
+// A batch solved as one system (offsets off[0..nsys], system j in rows
+// [off[j], off[j+1])): inside the tile of rows [ts, te), zero the couplings
+// across system boundaries, a of every system's first row and c of every
+// system's last row.  Warp 0 only; jb = warp_lower_bound(off, 1, nsys, ts).
+template <typename S>
+__device__ __forceinline__ void vtile_cut(int64_t ts, int64_t te, int s, int ldv, const int64_t* off, int32_t nsys,
+                                          int jb, S* A, S* C) {
+  constexpr int V = Vec<S>::W;
+  auto pos = [&](int64_t p) {
+    const int q = int(p - ts), t = q / s, j = q - t * s;
+    return ((j / V) * ldv + t) * V + j % V;
+  };
+  for (int j = jb + (threadIdx.x & 31); j < nsys; j += 32) {
+    const int64_t p = off[j];
+    if (p > te) break;
+    if (p < te) A[pos(p)] = S(0);
+    if (p - 1 >= ts) C[pos(p - 1)] = S(0);
+  }
 }
 
 // Planes of the tile to global arrays (16-byte stores, element-wise at the end).
@@ -230,6 +280,7 @@ __global__ void __launch_bounds__(256) k_stage1_v(const S* __restrict__ a, const
                                                   int64_t m, double* __restrict__ ra, double* __restrict__ rb,
                                                   double* __restrict__ rc, double* __restrict__ rd,
                                                   C* __restrict__ ka, C* __restrict__ kg, C* __restrict__ kd,
+                                                  const int64_t* __restrict__ off, int32_t nsys,
                                                   unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x, ldv = T + 1;
@@ -241,8 +292,15 @@ __global__ void __launch_bounds__(256) k_stage1_v(const S* __restrict__ a, const
   S* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};
   const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
   const S* const src[4] = {a, b, c, d};
-  vtile_load<S, 4>(ts, te, n, s, ldv, src, pl);
+  vtile_issue<S, 4>(ts, te, n, s, ldv, src, pl);
+  int jb = 0;
+  if (off && t < 32) jb = warp_lower_bound(off, 1, nsys, ts);  // while the copies fly
+  cp_async_commit_wait_all();
   __syncthreads();
+  if (off) {
+    if (t < 32) vtile_cut<S>(ts, te, s, ldv, off, nsys, jb, pl[0], pl[2]);
+    __syncthreads();
+  }
   if (t < nb) {
     const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
     IfaceRows r;
@@ -273,7 +331,8 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_stage3_resolve_v(const S* __restrict__ a, const S* __restrict__ b,
                                                           const S* __restrict__ c, const S* __restrict__ d,
                                                           int64_t n, int s, int64_t m, const double* __restrict__ y,
-                                                          S* __restrict__ x, unsigned* __restrict__ status) {
+                                                          S* __restrict__ x, const int64_t* __restrict__ off,
+                                                          int32_t nsys, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x, ldv = T + 1;
   const int64_t k0 = int64_t(blockIdx.x) * T;
@@ -284,8 +343,15 @@ __global__ void __launch_bounds__(256) k_stage3_resolve_v(const S* __restrict__ 
   S* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};
   const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
   const S* const src[4] = {a, b, c, d};
-  vtile_load<S, 4>(ts, te, n, s, ldv, src, pl);
+  vtile_issue<S, 4>(ts, te, n, s, ldv, src, pl);
+  int jb = 0;
+  if (off && t < 32) jb = warp_lower_bound(off, 1, nsys, ts);
+  cp_async_commit_wait_all();
   __syncthreads();
+  if (off) {
+    if (t < 32) vtile_cut<S>(ts, te, s, ldv, off, nsys, jb, pl[0], pl[2]);
+    __syncthreads();
+  }
   if (t < nb) {
     const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
     const double2 v = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));

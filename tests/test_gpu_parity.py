@@ -499,3 +499,43 @@ def test_tuning_variants(tdp, key, value):
                     assert e <= TOL[code], (key, value, n, code, s, e)
     finally:
         tdp.tdp_set_tuning(k, old)
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_batched_as_one_system(tdp, code):
+    """Batches of large systems are solved as one block-diagonal system
+    (couplings across system boundaries cut inside the tiles, or zeroed
+    copies for the refinement); blocks straddle boundaries, empty and
+    one-row systems sit between large ones.  The same batch with the block
+    map (TUNE_BATCH_FLAT = 0) must agree."""
+    import torch
+
+    sizes = [5000, 1, 0, 8193, 4096, 12000, 2, 7, 9999, 3, 6500]
+    Sb = W.batched(sizes=sizes, seed=11)
+    assert Sb.n >= 4096 * len(sizes)
+    ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+    dt = torch.float32 if code == 1 else torch.float64
+    a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+    # the ignored entries a[first row], c[last row] of every system hold garbage
+    for j in range(len(sizes)):
+        lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
+        if hi > lo:
+            a[lo] = 3.5
+            c[hi - 1] = -2.25
+    off = dev(Sb.offsets)
+    old = tdp.tdp_get_tuning(tdp.TUNE_BATCH_FLAT)
+    try:
+        for flat in (1, 0):
+            tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, flat)
+            for s in (0, 4, 8, 12, 24, 100):
+                x = torch.empty_like(d)
+                tdp.tdp_solve_batched(off, len(sizes), Sb.n, a, b, c, d, x, s, code, 1 if code == 2 else 0)
+                torch.cuda.synchronize()
+                got = host(x)
+                for j in range(len(sizes)):
+                    lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
+                    if hi > lo:
+                        e = oracle.rel_err(got[lo:hi], ref[lo:hi])
+                        assert e <= TOL[code], (flat, s, j, e)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, old)
