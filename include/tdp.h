@@ -76,12 +76,18 @@ int tdp_solve(const void* a, const void* b, const void* c, const void* d, void* 
  *               needed; the device checks it and reports TDP_EINVAL through
  *               the status word when it disagrees).
  *  s          : sub-system size for every system (2..1024), or 0 for the
- *               size model's choice for the mean system size and the batch
- *               size (tdp_predict_s); with the tuning key
- *               TDP_TUNE_PER_SYSTEM_S = 1, s = 0 instead gives every system
- *               its own size on the device (tdp_predict_s_batched), capped at
- *               the largest size the model gives for the nearest batch size.
- * Empty systems are allowed.  Other arguments as tdp_solve. */
+ *               size model's choice: a batch of at least 4096 rows per system
+ *               on average is solved as one block-diagonal system of total_n
+ *               rows (the couplings between systems are cut on the device;
+ *               TDP_TUNE_BATCH_FLAT) and s = 0 takes tdp_predict_s(total_n, 1,
+ *               dtype); otherwise blocks never straddle systems and s = 0
+ *               takes the size model for the mean system size and the batch
+ *               size.  With the tuning key TDP_TUNE_PER_SYSTEM_S = 1, s = 0
+ *               gives every system its own size on the device
+ *               (tdp_predict_s_batched), capped at the largest size the model
+ *               gives for the nearest batch size.
+ * Empty systems are allowed; a[offsets[j]] and c[offsets[j+1]-1] are ignored.
+ * Other arguments as tdp_solve. */
 int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                       const void* c, const void* d, void* x, int32_t s, tdp_dtype dtype, int32_t refine_iters,
                       void* stream);

@@ -184,8 +184,10 @@ int run(void* stream, const char* fn, F&& driver) {
   ctx.stream = st;
   ctx.status = ws->status;
   ctx.ar = &arena;
+  arena.err = &ctx.err;
   driver(ctx);
-  if (ctx.err != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + ctx.msg);
+  if (ctx.err != cudaSuccess)
+    return set_error(TDP_ECUDA, std::string(fn) + ": " + (ctx.msg.empty() ? "workspace overrun" : ctx.msg));
   if (g_checked.load()) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));

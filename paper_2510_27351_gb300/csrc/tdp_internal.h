@@ -13,16 +13,26 @@
 namespace tdp {
 
 // Bump allocator over a workspace buffer.  With base == nullptr it only
-// measures (dry run used to size the workspace before any launch).
+// measures (dry run used to size the workspace before any launch).  The real
+// run takes exactly what the dry run measured; should it ask for more, the
+// take raises *err (so that no further kernel launches) and hands back the
+// start of the buffer instead of memory past its end.
 struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t off = 0;
+  cudaError_t* err = nullptr;
   template <typename T>
   T* take(size_t count) {
     off = (off + 255) & ~size_t(255);
+    const size_t bytes = count * sizeof(T) + 16;
+    if (base && off + bytes > cap) {
+      if (err && *err == cudaSuccess) *err = cudaErrorMemoryAllocation;
+      off += bytes;
+      return reinterpret_cast<T*>(base);
+    }
     T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-    off += count * sizeof(T) + 16;
+    off += bytes;
     return p;
   }
 };

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(256) k_stage1(const S* __restrict__ a, const S
                                                 double* __restrict__ ra, double* __restrict__ rb,
                                                 double* __restrict__ rc, double* __restrict__ rd,
                                                 C* __restrict__ oa, C* __restrict__ og, C* __restrict__ od,
+                                                const int64_t* __restrict__ off, int32_t nsys,
                                                 unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, ld = T + 1, t = threadIdx.x;
@@ -288,12 +289,18 @@ __global__ void __launch_bounds__(256) k_stage1(const S* __restrict__ a, const S
     if (t < nb) fill_owner(own, t, int(bi.start - g.ts), bi.len);
     __syncthreads();
   }
+  int jb = 0;
+  if (!MAPPED && off && t < 32) jb = warp_lower_bound(off, 1, nsys, g.ts);  // batch solved as one system
   {
     const S* src[4] = {a, b, c, d};
     C* dst[4] = {sA, sB, sC, sD};
     tile_load<S, C, MAPPED, 4>(g, src, dst, n);
   }
   __syncthreads();
+  if (!MAPPED && off) {
+    if (t < 32) tile_cut<C>(g, off, nsys, jb, sA, sC, nullptr, nullptr);
+    __syncthreads();
+  }
   if (t < nb) {
     IfaceRows r;
     if constexpr (std::is_same<C, float>::value && !KEEP)

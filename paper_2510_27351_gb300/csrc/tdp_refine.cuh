@@ -103,8 +103,9 @@ __device__ __forceinline__ void refine_mid_reduce(const TileGeom& g, float* sA, 
 // Pass 2 (see above).  Shared memory: five binary32 planes of s * (T + 1)
 // rows (a, b, c, d -> x0, gamma -> r), plus the owner table when mapped.
 // KEPT: x0 goes to x0f (binary32) and the correction's kept coefficients to
-// (ka, kg, kd); x and rr are not written.
-template <bool MAPPED, bool KEPT>
+// (ka, kg, kd); x and rr are not written.  FLAT (one system's tiles only): a
+// batch solved as one system, boundaries in off[1..nsys-1].
+template <bool MAPPED, bool KEPT, bool FLAT>
 __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a, const double* __restrict__ b,
                                                     const double* __restrict__ c, const double* __restrict__ d,
                                                     double* __restrict__ x, float* __restrict__ rr, int64_t n, int s,
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
                                                     double* __restrict__ rc, double* __restrict__ rd,
                                                     float* __restrict__ x0f, float* __restrict__ ka,
                                                     float* __restrict__ kg, float* __restrict__ kd,
+                                                    const int64_t* __restrict__ off, int32_t nsys,
                                                     unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, ld = T + 1, t = threadIdx.x;
@@ -128,11 +130,25 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
   float* sG = sD + plane;
   uint32_t* own = reinterpret_cast<uint32_t*>(sG + plane);
   TileGeom g{block_start<MAPPED>(k0, n, s, blk), block_start<MAPPED>(k0 + nb, n, s, blk), s, magic, ld, own};
+  const int rows = int(g.te - g.ts);
+  // FLAT: rows that start (fst) or end (fen) a system, one byte each after
+  // the planes, built only in tiles that hold a system boundary (flat)
+  static_assert(!(FLAT && MAPPED), "block-mapped tiles never straddle systems");
+  __shared__ int s_cut;
+  uint8_t* fst = reinterpret_cast<uint8_t*>(sG + plane);
+  uint8_t* fen = fst + size_t(T) * s;
   BlockInfo bi{0, 0, false, false};
   if (t < nb) bi = block_info<MAPPED>(k0 + t, n, s, m, blk);
   if constexpr (MAPPED) {
     if (t < nb) fill_owner(own, t, int(bi.start - g.ts), bi.len);
     __syncthreads();
+  }
+  int jb = 0;
+  if constexpr (FLAT) {
+    if (t < 32) {
+      jb = warp_lower_bound(off, 1, nsys, g.ts);
+      if (t == 0) s_cut = (jb < nsys && off[jb] <= g.te) ? 1 : 0;
+    }
   }
   {
     const double* src[4] = {a, b, c, d};
@@ -140,14 +156,22 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
     tile_load<double, float, MAPPED, 4>(g, src, dst, n);
   }
   __syncthreads();
+  const bool flat = FLAT && s_cut;
+  if (flat) {
+    for (int q = t; q < rows; q += T) { fst[q] = 0; fen[q] = 0; }
+    __syncthreads();
+    if (t < 32) tile_cut<float>(g, off, nsys, jb, sA, sC, fst, fen);
+    __syncthreads();
+  }
   if (t < nb) {
     const double2 v = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));
     lean_substitute(sA + t, sB + t, sC + t, sD + t, sG + t, ld, bi.len, narrow(v.x), narrow(v.y), status);
   }
   __syncthreads();
   // residual, one row per thread in memory order; the neighbours of the
-  // tile's end rows are interface values of the neighbouring blocks
-  const int rows = int(g.te - g.ts);
+  // tile's end rows are interface values of the neighbouring blocks.  A row
+  // that starts a system has no left neighbour term, one that ends a system
+  // no right neighbour term.
   const float x_before = k0 > 0 ? narrow(y[2 * k0 - 1]) : 0.0f;
   const float x_after = k0 + nb < m ? narrow(y[2 * (k0 + nb)]) : 0.0f;
   if (!MAPPED && s % 2 == 0) {
@@ -184,11 +208,13 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
         if (two) {
           const double2 va = la[u], vb = lb[u], vc = lc[u], vd = ldd[u];
           const double w0 = widen(x0), w1 = widen(x1);
+          bool s0 = false, e0 = false, s1 = false, e1 = false;
+          if (flat) { s0 = fst[p]; e0 = fen[p]; s1 = fst[p + 1]; e1 = fen[p + 1]; }
           double r0 = fma(-vb.x, w0, vd.x), r1 = fma(-vb.y, w1, vd.y);
-          r0 = fma(-vc.x, w1, r0);
-          r1 = fma(-va.y, w0, r1);
-          if (i > 0) r0 = fma(-va.x, widen(xp), r0);
-          if (i + 2 < n) r1 = fma(-vc.y, widen(xn), r1);
+          if (!e0) r0 = fma(-vc.x, w1, r0);
+          if (!s1) r1 = fma(-va.y, w0, r1);
+          if (i > 0 && !s0) r0 = fma(-va.x, widen(xp), r0);
+          if (i + 2 < n && !e1) r1 = fma(-vc.y, widen(xn), r1);
           const float f0 = narrow(r0), f1 = narrow(r1);
           if constexpr (KEPT) {
             *reinterpret_cast<float2*>(x0f + i) = make_float2(x0, x1);
@@ -201,7 +227,7 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
         } else {  // the last row of the system
           const double w0 = widen(x0);
           double r0 = fma(-b[i], w0, d[i]);
-          if (i > 0) r0 = fma(-a[i], widen(xp), r0);
+          if (i > 0 && !(flat && fst[p])) r0 = fma(-a[i], widen(xp), r0);
           const float f0 = narrow(r0);
           if constexpr (KEPT) {
             x0f[i] = x0;
@@ -231,6 +257,7 @@ __global__ void __launch_bounds__(256) k_refine_mid(const double* __restrict__ a
         lc[u] = c[i];
         ldd[u] = d[i];
         le[u] = MAPPED ? edge[i] : uint8_t((i == 0 ? 1 : 0) | (i == n - 1 ? 2 : 0));
+        if (flat) le[u] |= uint8_t(fst[p] | (fen[p] << 1));
       }
     }
 #pragma unroll

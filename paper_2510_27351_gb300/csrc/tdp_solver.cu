@@ -38,7 +38,10 @@ void allow_smem(K kernel) {
   const std::pair<int, const void*> key{dev, reinterpret_cast<const void*>(kernel)};
   std::lock_guard<std::mutex> lk(mu);
   if (done.count(key)) return;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  // the per-CTA limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa{};
+  const int stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? int(fa.sharedSizeBytes) : 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - stat);
   done.insert(key);
 }
 
@@ -265,6 +268,7 @@ WCfg wtile_cfg(K kern, int s, int64_t m) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+
 template <typename S, typename C, bool MAPPED, bool KEEP>
 void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
             const int64_t* blk, double* ra, double* rb, double* rc, double* rd, C* ka, C* kg, C* kd,
@@ -325,7 +329,7 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
   const int64_t grid = (m + T - 1) / T;
   pre_launch(ctx, nm);
   kern<<<unsigned(grid), T, smem, ctx.stream>>>(a, b, c, d, n, s, magic_for(s), m, blk, ra, rb, rc, rd, ka, kg,
-                                                kd, ctx.status);
+                                                kd, MAPPED ? nullptr : ctx.flat_off, ctx.flat_nsys, ctx.status);
   post_launch(ctx, "stage 1");
 }
 
@@ -936,11 +940,15 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
     if (!ctx.dry && ctx.err == cudaSuccess) {
       size_t smem;
       const int T = pick_threads(ctx, s, 5, 4, MAPPED, &smem);
-      auto kern = kept ? k_refine_mid<MAPPED, true> : k_refine_mid<MAPPED, false>;
+      const int64_t* foff = MAPPED ? nullptr : ctx.flat_off;
+      if (foff) smem += size_t(2) * T * s;  // row flags of a batch solved as one system
+      auto kern = kept ? (foff ? k_refine_mid<MAPPED, true, !MAPPED> : k_refine_mid<MAPPED, true, false>)
+                       : (foff ? k_refine_mid<MAPPED, false, !MAPPED> : k_refine_mid<MAPPED, false, false>);
       allow_smem(kern);
       pre_launch(ctx, "refine_mid");
       kern<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(A, B, Cc, D, X, rr, n, s, magic_for(s), m, blk, edge,
-                                                               y, ra, rb, rc, rd, x0f, fka, fkg, fkd, ctx.status);
+                                                               y, ra, rb, rc, rd, x0f, fka, fkg, fkd, foff,
+                                                               ctx.flat_nsys, ctx.status);
       post_launch(ctx, "refine pass 2");
     }
     solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
@@ -1218,8 +1226,23 @@ struct FlatScope {
   }
 };
 
-// a2 = a, c2 = c with a of every system's first row and c of its last row
-// set to zero (the diagonals as one block-diagonal system).
+// a2 = a, c2 = c (16-byte copies; a kernel rather than two device-to-device
+// copies, which a CUDA graph would run on the copy engines).
+__global__ void k_copy2(const double* __restrict__ a, const double* __restrict__ c, double* __restrict__ a2,
+                        double* __restrict__ c2, int64_t n) {
+  const int64_t pairs = n / 2;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < pairs; q += int64_t(gridDim.x) * blockDim.x) {
+    reinterpret_cast<double2*>(a2)[q] = __ldcs(reinterpret_cast<const double2*>(a) + q);
+    reinterpret_cast<double2*>(c2)[q] = __ldcs(reinterpret_cast<const double2*>(c) + q);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
+    a2[n - 1] = a[n - 1];
+    c2[n - 1] = c[n - 1];
+  }
+}
+
+// With a of every system's first row and c of its last row set to zero the
+// copies are the diagonals of one block-diagonal system.
 template <typename S>
 __global__ void k_cut_edges(const int64_t* __restrict__ off, int32_t batch, S* __restrict__ a2, S* __restrict__ c2) {
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < batch; j += int64_t(gridDim.x) * blockDim.x) {
@@ -1235,10 +1258,12 @@ __global__ void k_cut_edges(const int64_t* __restrict__ off, int32_t batch, S* _
 // couplings across system boundaries are zero (a block-diagonal tridiagonal
 // system): the single-system tiles (16-byte cp.async, no block map) then
 // serve batches too.  Blocks may straddle a boundary; elimination across a
-// zero coupling is exact.  Binary64 and binary32 cut the couplings inside the
-// interleaved tiles, which requires those tiles for every kernel that reads
-// a and c; the refinement (whose passes read a and c in several layouts)
-// works on copies of a and c with the couplings zeroed.
+// zero coupling is exact.  The kernels that read a and c cut the couplings
+// inside their tiles (k_stage1_v, k_stage3_resolve_v, k_stage1, and
+// k_refine_mid, which also drops the cross-boundary terms of its residual),
+// so every kernel of the chosen schedule must be one of them; refinement
+// schedules with other kernels work on copies of a and c with the couplings
+// zeroed.
 bool flat_batch(const Ctx& ctx, int32_t batch, int64_t total_n, tdp_dtype dt, int s) {
   if (!ctx.batch_flat || batch < 2 || total_n < int64_t(batch) * 4096) return false;
   if (dt == TDP_F32_REFINE) return true;
@@ -1250,7 +1275,10 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
                 const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
   if (s > total_n) s = int(std::max<int64_t>(2, total_n));
   const int64_t m = (total_n + s - 1) / s;
-  if (dt != TDP_F32_REFINE) {
+  const bool cut_in_tiles = dt != TDP_F32_REFINE ||
+                            (refine_iters == 1 && ctx.refine3 && ctx.refine_kept && !ctx.fused_refine &&
+                             !ctx.wtile && !ctx.tma && !ctx.pipeline);
+  if (cut_in_tiles) {
     FlatScope fs(ctx, offsets, batch);
     solve_blocks<false>(ctx, a, b, c, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);
     return;
@@ -1258,8 +1286,10 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
   double* a2 = ctx.ar->take<double>(total_n);
   double* c2 = ctx.ar->take<double>(total_n);
   if (!ctx.dry && ctx.err == cudaSuccess) {
-    ctx.fail(cudaMemcpyAsync(a2, a, size_t(total_n) * 8, cudaMemcpyDeviceToDevice, ctx.stream), "copy of a");
-    ctx.fail(cudaMemcpyAsync(c2, c, size_t(total_n) * 8, cudaMemcpyDeviceToDevice, ctx.stream), "copy of c");
+    pre_launch(ctx, "copy_ac");
+    k_copy2<<<grid_for(total_n / 2 + 1, 256), 256, 0, ctx.stream>>>((const double*)a, (const double*)c, a2, c2,
+                                                                   total_n);
+    post_launch(ctx, "copy of a and c");
     pre_launch(ctx, "cut_edges");
     k_cut_edges<double><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, a2, c2);
     post_launch(ctx, "cut edges");

@@ -30,6 +30,55 @@ __device__ __forceinline__ void owner(const TileGeom& g, int p, int& t, int& j) 
   }
 }
 
+// Smallest j in [lo, hi) with off[j] >= key (hi if none), off non-decreasing;
+// all 32 lanes of a warp call it.  Each round probes 32 evenly spaced entries
+// at once, so a batch of B systems takes about log32(B) dependent loads.
+__device__ __forceinline__ int warp_lower_bound(const int64_t* off, int lo, int hi, int64_t key) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int j = lo + lane * step;
+    const bool ge = (j >= hi) || off[j] >= key;
+    const unsigned msk = __ballot_sync(0xffffffffu, ge);
+    const int f = msk ? __ffs(msk) - 1 : 32;
+    if (f == 0) return lo;
+    // probe f-1 is below key, probe f (if any) at or above it
+    const int nlo = lo + (f - 1) * step + 1;
+    hi = min(hi, lo + f * step);
+    lo = nlo;
+  }
+  const int j = lo + lane;
+  const bool ge = (j >= hi) || off[j] >= key;
+  const unsigned msk = __ballot_sync(0xffffffffu, ge);
+  return msk ? lo + __ffs(msk) - 1 : hi;
+}
+
+// A batch solved as one system (system j in rows [off[j], off[j+1])): in the
+// tile of rows [g.ts, g.te), zero a of every system's first row and c of every
+// system's last row, and, with fst/fen, mark those rows (byte per tile row,
+// zeroed by the caller).  Warp 0 only; jb = warp_lower_bound(off, 1, nsys,
+// g.ts).  Two flag arrays, so that neighbouring boundaries never update the
+// same byte.
+template <typename C>
+__device__ __forceinline__ void tile_cut(const TileGeom& g, const int64_t* off, int32_t nsys, int jb, C* A, C* Cc,
+                                         uint8_t* fst, uint8_t* fen) {
+  for (int j = jb + (threadIdx.x & 31); j < nsys; j += 32) {
+    const int64_t p = off[j];
+    if (p > g.te) break;
+    int t, jj;
+    if (p < g.te) {
+      owner<false>(g, int(p - g.ts), t, jj);
+      A[jj * g.ld + t] = C(0);
+      if (fst) fst[p - g.ts] = 1;
+    }
+    if (p - 1 >= g.ts) {
+      owner<false>(g, int(p - 1 - g.ts), t, jj);
+      Cc[jj * g.ld + t] = C(0);
+      if (fen) fen[p - 1 - g.ts] = 1;
+    }
+  }
+}
+
 // Load NA arrays of storage type S (n_arr valid elements each) for rows
 // [ts, te) into shared tiles of compute type C.  When blocks start on vector
 // boundaries (one system, s a multiple of V) a vector never straddles two

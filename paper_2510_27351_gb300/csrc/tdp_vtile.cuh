@@ -55,29 +55,6 @@ __device__ __forceinline__ void vtile_load(int64_t ts, int64_t te, int64_t n, in
   cp_async_commit_wait_all();
 }
 
-// Smallest j in [lo, hi) with off[j] >= key (hi if none), off non-decreasing;
-// all 32 lanes of a warp call it.  Each round probes 32 evenly spaced entries
-// at once, so a batch of B systems takes about log32(B) dependent loads.
-__device__ __forceinline__ int warp_lower_bound(const int64_t* off, int lo, int hi, int64_t key) {
-  const int lane = threadIdx.x & 31;
-  while (hi - lo > 32) {
-    const int step = (hi - lo + 31) >> 5;
-    const int j = lo + lane * step;
-    const bool ge = (j >= hi) || off[j] >= key;
-    const unsigned msk = __ballot_sync(0xffffffffu, ge);
-    const int f = msk ? __ffs(msk) - 1 : 32;
-    if (f == 0) return lo;
-    // probe f-1 is below key, probe f (if any) at or above it
-    const int nlo = lo + (f - 1) * step + 1;
-    hi = min(hi, lo + f * step);
-    lo = nlo;
-  }
-  const int j = lo + lane;
-  const bool ge = (j >= hi) || off[j] >= key;
-  const unsigned msk = __ballot_sync(0xffffffffu, ge);
-  return msk ? lo + __ffs(msk) - 1 : hi;
-}
-
 // A batch solved as one system (offsets off[0..nsys], system j in rows
 // [off[j], off[j+1])): inside the tile of rows [ts, te), zero the couplings
 // across system boundaries, a of every system's first row and c of every

@@ -525,17 +525,19 @@ def test_batched_as_one_system(tdp, code):
     off = dev(Sb.offsets)
     old = tdp.tdp_get_tuning(tdp.TUNE_BATCH_FLAT)
     try:
-        for flat in (1, 0):
+        # refinement: one correction cuts inside the tiles, two work on zeroed copies
+        runs = [(flat, s, it) for flat in (1, 0) for s in (0, 4, 8, 12, 24, 100)
+                for it in ((1, 2) if code == 2 else (0,))]
+        for flat, s, it in runs:
             tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, flat)
-            for s in (0, 4, 8, 12, 24, 100):
-                x = torch.empty_like(d)
-                tdp.tdp_solve_batched(off, len(sizes), Sb.n, a, b, c, d, x, s, code, 1 if code == 2 else 0)
-                torch.cuda.synchronize()
-                got = host(x)
-                for j in range(len(sizes)):
-                    lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
-                    if hi > lo:
-                        e = oracle.rel_err(got[lo:hi], ref[lo:hi])
-                        assert e <= TOL[code], (flat, s, j, e)
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(off, len(sizes), Sb.n, a, b, c, d, x, s, code, it)
+            torch.cuda.synchronize()
+            got = host(x)
+            for j in range(len(sizes)):
+                lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
+                if hi > lo:
+                    e = oracle.rel_err(got[lo:hi], ref[lo:hi])
+                    assert e <= TOL[code], (flat, s, it, j, e)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, old)
