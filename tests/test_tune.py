@@ -105,3 +105,29 @@ def test_recursion_depth_table_and_evaluation():
     assert rep["n_sizes"] == 12 and 0.0 <= rep["accuracy"] <= 1.0
     assert rep["mean_time_loss"] >= 0.0
     assert all(abs(v - 1.0 / 1.05) < 1e-12 for v in rep["best_over_default_all"].values())
+
+
+def test_precision_transfer_study_on_synthetic_sweeps():
+    """evaluate_transfer: a source precision with the same timings as the
+    target transfers perfectly; one whose optimum is shifted loses exactly the
+    target's time ratio at every size."""
+    from paper_2510_27351_gb300 import tune
+
+    sizes = [1 << k for k in range(10, 20)]
+    rows = []
+    for n in sizes:
+        for s in (8, 16, 32):
+            t_a = 1.0 + abs(s - 16) / 16          # optimum 16 for dtypes 0 and 1
+            t_c = 1.0 + abs(s - 32) / 32          # optimum 32 for dtype 2
+            rows += [{"dtype": 0, "n": n, "batch": 1, "s": s, "ms": t_a},
+                     {"dtype": 1, "n": n, "batch": 1, "s": s, "ms": t_a},
+                     {"dtype": 2, "n": n, "batch": 1, "s": s, "ms": t_c}]
+    rep = tune.evaluate_transfer(rows)
+    same = rep["f64->f32/batch1"]
+    assert same["accuracy"] == 1.0 and same["mean_time_loss"] == 0.0
+    shifted = rep["f64->f32_refine/batch1"]
+    assert shifted["accuracy"] == 0.0
+    assert shifted["mean_time_loss"] == pytest.approx(1.5 - 1.0)  # s = 16 on a target whose best is 32
+    assert shifted["best_fixed_s"] == 32 and shifted["target_loo_mean_time_loss"] == 0.0
+    assert set(rep) == {f"{a}->{b}/batch1" for a in ("f64", "f32", "f32_refine")
+                        for b in ("f64", "f32", "f32_refine") if a != b}
