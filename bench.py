@@ -467,6 +467,25 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
     out["adjoint_1024x8192"] = {"ms": ms, "unknowns_per_s": Sa.n / (ms * 1e-3),
                                 "hbm_frac_72B": hbm(ms, 72 * Sa.n)}
     del adev, ax, grads
+    # many right-hand sides of one matrix: 16 columns of a 2^22-row system,
+    # one factorisation, against the same columns as 16 separate solves
+    nm, km = 1 << 22, 16
+    Sm = W.single(nm, seed=3)
+    mdev = {k: torch.from_numpy(getattr(Sm, k)).to(device) for k in ("a", "b", "c")}
+    Dm = torch.from_numpy(W.rhs_columns(nm, km, seed=3).reshape(-1)).to(device)
+    Xm = torch.empty_like(Dm)
+    fn = lambda: tdp.tdp_solve_multi(mdev["a"], mdev["b"], mdev["c"], Dm, Xm, nm, km, nm, nm, 0, tdp.F64, stream)
+    ms = cuda_time(fn, steps, 2, stream)
+
+    def separate():
+        for j in range(km):
+            tdp.tdp_solve(mdev["a"], mdev["b"], mdev["c"], Dm[j * nm:(j + 1) * nm], Xm[j * nm:(j + 1) * nm], nm, 0,
+                          tdp.F64, 0, stream)
+
+    ms_sep = cuda_time(separate, max(3, steps // 4), 1, stream)
+    out["multi_rhs_2^22x16"] = {"ms": ms, "unknowns_per_s": km * nm / (ms * 1e-3), "separate_solves_ms": ms_sep,
+                                "s": min(64, max(16, 4 * tdp.tdp_predict_s(nm, 1, tdp.F64))), "dtype": "f64"}
+    del mdev, Dm, Xm
     # implicit heat step on 2048^2: row sweep then column sweep
     H = W.heat(2048, 0.5, seed=0)
     hd = {k: torch.from_numpy(np.ascontiguousarray(getattr(H, k)).reshape(-1)).to(device) for k in ("a", "b", "c", "u")}

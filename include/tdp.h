@@ -109,6 +109,23 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
                     int64_t sys_stride, int64_t elem_stride, int32_t s, tdp_dtype dtype, int32_t refine_iters,
                     void* stream);
 
+/* Many right-hand sides with one matrix (not in the paper): solve A X = D for
+ * nrhs columns of n unknowns.  Column j of D starts at element j*ldd of d, column
+ * j of X at element j*ldx of x (ldd, ldx >= n; the X and D ranges must not
+ * overlap).  The matrix part of the method (reciprocal pivots, multipliers, the
+ * spike and backward coefficients of Stage 3 and the interface matrix, Sec. I)
+ * is computed once; each column then costs the d-part of Stage 1 and Stage 3
+ * (5 operations per row instead of 14) and its share of one interface solve over
+ * all columns.  dtype TDP_F64 or TDP_F32 (a, b, c, d, x of that type); s in
+ * [2, 1024], or 0 for four times tdp_predict_s(n, 1, dtype) within [16, 64]
+ * (a column skips the matrix part, so the interface solve weighs more and a
+ * larger s pays); 1 <= nrhs <= 65535.  All
+ * pointers 16-byte aligned and every column too (ldd, ldx multiples of 16
+ * bytes), else TDP_EINVAL.  Scratch: 5n words for the matrix part plus the
+ * interface systems. */
+int tdp_solve_multi(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t nrhs,
+                    int64_t ldd, int64_t ldx, int32_t s, tdp_dtype dtype, void* stream);
+
 /* Solve `batch` systems of n unknowns each with arbitrary element strides:
  * element i of system j lives at index  j*sys_stride + i*elem_stride  of each
  * array (in elements).  sys_stride = n, elem_stride = 1 is a contiguous batch;

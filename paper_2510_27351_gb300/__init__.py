@@ -34,8 +34,10 @@ class TdpError(RuntimeError):
 
 def _load() -> ctypes.CDLL:
     path = _build.LIB
-    if not os.path.exists(path) or os.environ.get("TDP_REBUILD") == "1":
-        _build.build()
+    sources = [os.path.join(_build.CSRC, f) for f in os.listdir(_build.CSRC)] + [
+        os.path.join(_build.ROOT, "include", "tdp.h")]
+    if os.environ.get("TDP_REBUILD") == "1" or _build._stale(path, sources):
+        _build.build()  # incremental: only stale translation units are compiled
     lib = ctypes.CDLL(path)
     P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     lib.tdp_solve.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
@@ -68,6 +70,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_load_rtable.argtypes = [ctypes.c_char_p]
     lib.tdp_recursion_plan.argtypes = [I64, I32, I32, I32, P, I32]
     lib.tdp_recursion_plan.restype = I32
+    lib.tdp_solve_multi.argtypes = [P, P, P, P, P, I64, I32, I64, I64, I32, I32, P]
     return lib
 
 
@@ -78,7 +81,7 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
-           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const")
+           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
  TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S,
@@ -174,6 +177,12 @@ def tdp_load_table(path: str):
 def tdp_solve_const(a, b, c, d, x, n, batch, sys_stride, elem_stride, s, dtype, refine_iters=0, stream=None):
     _check(LIB.tdp_solve_const(float(a), float(b), float(c), _ptr(d), _ptr(x), int(n), int(batch), int(sys_stride),
                                int(elem_stride), int(s), int(dtype), int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_multi(a, b, c, d, x, n, nrhs, ldd, ldx, s=0, dtype=F64, stream=None):
+    """A X = D for nrhs columns (column j of d / x at element j*ldd / j*ldx)."""
+    _check(LIB.tdp_solve_multi(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), int(n), int(nrhs), int(ldd), int(ldx),
+                               int(s), int(dtype), _stream(stream)))
 
 
 def tdp_predict_r(n: int, batch: int = 1, dtype: int = F64) -> int:

@@ -116,6 +116,8 @@ int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);
 int32_t predict_r(int64_t n, int32_t batch, tdp_dtype dt);
 int load_rtable_file(const char* path);
 int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap);
+void solve_multi(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                 int32_t nrhs, int64_t ldd, int64_t ldx, int s, tdp_dtype dt);
 // Flattened table for the device-side predictor: rows of (log2 n, log2 batch, s) per dtype.
 int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels);
 

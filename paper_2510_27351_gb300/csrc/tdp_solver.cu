@@ -18,6 +18,7 @@
 #include "tdp_wtile.cuh"
 #include "tdp_refine.cuh"
 #include "tdp_const.cuh"
+#include "tdp_multi.cuh"
 
 namespace tdp {
 
@@ -1187,6 +1188,74 @@ void solve_const(Ctx& ctx, double a, double b, double c, const void* d, void* x,
       }
     }
   }
+}
+
+template <typename S, typename C>
+void multi_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int32_t nrhs, int64_t ldd,
+                int64_t ldx, int s) {
+  const int64_t m = (n + s - 1) / s, M = 2 * m;
+  double* ra = ctx.ar->take<double>(M);
+  double* rb = ctx.ar->take<double>(M);
+  double* rc = ctx.ar->take<double>(M);
+  double* A = nrhs > 1 ? ctx.ar->take<double>(M * nrhs) : ra;
+  double* B = nrhs > 1 ? ctx.ar->take<double>(M * nrhs) : rb;
+  double* Cc = nrhs > 1 ? ctx.ar->take<double>(M * nrhs) : rc;
+  double* rd = ctx.ar->take<double>(M * nrhs);
+  double* y = ctx.ar->take<double>(M * nrhs);
+  C* rT = ctx.ar->take<C>(size_t(s) * m);  // transposed: row j of block k at j * m + k
+  C* qT = ctx.ar->take<C>(size_t(s) * m);
+  C* gT = ctx.ar->take<C>(size_t(s) * m);
+  C* ap = ctx.ar->take<C>(n);
+  C* gp = ctx.ar->take<C>(n);
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    size_t smem;
+    const int T = pick_threads(ctx, s, 3, sizeof(C), false, &smem);
+    auto kf = k_multi_factor<S, C>;
+    allow_smem(kf);
+    pre_launch(ctx, tname<C>("multi_factor_f64", "multi_factor_f32"));
+    kf<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, n, s, magic_for(s), m, rT, qT, gT, ap, gp, ra,
+                                                           rb, rc, ctx.status);
+    post_launch(ctx, "factor");
+    if (nrhs > 1) {
+      pre_launch(ctx, "multi_replicate");
+      k_multi_replicate<<<grid_for(M * nrhs, 256), 256, 0, ctx.stream>>>(ra, rb, rc, M, nrhs, A, B, Cc);
+      post_launch(ctx, "interface matrix copies");
+    }
+    size_t smem2;
+    const int T2 = pick_threads(ctx, s, 1, sizeof(C), false, &smem2);
+    auto kr = k_multi_reduce<S, C>;
+    allow_smem(kr);
+    pre_launch(ctx, tname<C>("multi_reduce_f64", "multi_reduce_f32"));
+    kr<<<dim3(unsigned((m + T2 - 1) / T2), unsigned(nrhs)), T2, smem2, ctx.stream>>>(rT, qT, gT, c, d, ldd, x, ldx,
+                                                                                     n, s, magic_for(s), m, rd);
+    post_launch(ctx, "right-hand sides, Stage 1");
+  }
+  {
+    // the columns' interface systems, one after another (decoupled copies);
+    // one CTA per column when they are small and many
+    SegScope seg(ctx, nullptr, m, nrhs);
+    solve_interface(ctx, A, B, Cc, rd, y, M * nrhs);
+  }
+  if (!ctx.dry && ctx.err == cudaSuccess) {
+    pre_launch(ctx, tname<C>("multi_stage3_f64", "multi_stage3_f32"));
+    k_multi_stage3<S, C><<<grid_for(n * nrhs, 256), 256, 0, ctx.stream>>>(ap, gp, x, ldx, n, s, m, nrhs, y);
+    post_launch(ctx, "right-hand sides, Stage 3");
+  }
+}
+
+void solve_multi(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
+                 int32_t nrhs, int64_t ldd, int64_t ldx, int s, tdp_dtype dt) {
+  ctx.rec_n = n;
+  ctx.rec_batch = 1;
+  ctx.rec_dt = dt;
+  if (n <= 0 || nrhs <= 0) return;
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  if (dt == TDP_F64)
+    multi_pass<double, double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d,
+                               (double*)x, n, nrhs, ldd, ldx, s);
+  else
+    multi_pass<float, float>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)d, (float*)x, n,
+                             nrhs, ldd, ldx, s);
 }
 
 int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap) {

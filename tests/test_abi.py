@@ -60,6 +60,17 @@ def test_bad_arguments_rejected_on_host():
     assert lib.tdp_solve_strided(2, 8, -1, 1, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
     # backward refuses the refinement dtype
     assert lib.tdp_solve_backward(16, 1, 8, 16, 16, 16, 16, 16, 0, 0, 0, 0, 4, 2, 0) == 1
+    # many right-hand sides: (a, b, c, d, x, n, nrhs, ldd, ldx, s, dtype, stream)
+    m = lib.tdp_solve_multi
+    assert m(16, 16, 16, 1 << 20, 1 << 24, 10, 0, 10, 10, 4, 0, 0) == 1      # nrhs < 1
+    assert m(16, 16, 16, 1 << 20, 1 << 24, 10, 2, 9, 10, 4, 0, 0) == 1       # ldd < n
+    assert m(16, 16, 16, 1 << 20, 1 << 24, 10, 2, 10, 10, 4, 2, 0) == 1      # refinement dtype
+    assert m(16, 16, 16, 1 << 20, (1 << 20) + 128, 10, 2, 10, 10, 4, 0, 0) == 1
+    assert "overlap" in tdp.tdp_last_error()
+    assert m(16, 16, 16, 1 << 20, (1 << 24) + 8, 10, 2, 10, 10, 4, 0, 0) == 1
+    assert "aligned" in tdp.tdp_last_error()
+    assert m(16, 16, 16, 1 << 20, 1 << 24, 11, 2, 11, 12, 4, 0, 0) == 1     # odd column stride
+    assert "16-byte" in tdp.tdp_last_error()
 
 
 def test_predictor_is_host_only_and_valid():

@@ -157,3 +157,21 @@ def test_binary64_interface_levels_2e26(tdp, single_full, code):
         test_single_system_2e26(tdp, single_full, code)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_IFACE32, old)
+
+
+def test_many_rhs_2e22x16(tdp):
+    """16 right-hand sides of one 2^22-row system (2^26 unknowns in all),
+    binary64, every element against the oracle."""
+    import torch
+
+    n, nrhs = 1 << 22, 16
+    S = W.single(n, seed=3)
+    D = W.rhs_columns(n, nrhs, seed=3)
+    a, b, c = (_dev(v, torch.float64) for v in (S.a, S.b, S.c))
+    d = _dev(D.reshape(-1), torch.float64)
+    x = torch.empty_like(d)
+    tdp.tdp_solve_multi(a, b, c, d, x, n, nrhs, n, n, 0, 0)
+    torch.cuda.synchronize()
+    X = x.cpu().numpy().reshape(nrhs, n)
+    for j in range(nrhs):
+        assert oracle.rel_err(X[j], oracle.thomas(S.a, S.b, S.c, D[j])) <= 1e-12, j

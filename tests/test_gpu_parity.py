@@ -541,3 +541,34 @@ def test_batched_as_one_system(tdp, code):
                     assert e <= TOL[code], (flat, s, it, j, e)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, old)
+
+
+@pytest.mark.parametrize("code", [0, 1])
+def test_many_rhs_vs_oracle(tdp, code):
+    """tdp_solve_multi: every column against the oracle's Thomas, ragged last
+    blocks, padded leading dimensions (d's padding holds nan, x's padding must
+    stay untouched), and a case with enough small columns for the per-column
+    interface solves."""
+    import torch
+
+    dt = torch.float32 if code == 1 else torch.float64
+    cases = [(n, nrhs, s) for n in (1, 2, 3, 5, 33, 1000, 4097, 100_003) for nrhs in (1, 3, 8)
+             for s in (2, 3, 8, 32, 100)] + [(200, 40, 8), (5000, 33, 16)]
+    for n, nrhs, s in cases:
+        S = W.single(n, seed=n)
+        D = W.rhs_columns(n, nrhs, seed=n)
+        v = 4 if code == 1 else 2  # columns start on 16-byte boundaries
+        ldd, ldx = -(-(n + 3) // v) * v, -(-(n + 5) // v) * v
+        dpad = np.full((nrhs, ldd), np.nan)
+        dpad[:, :n] = D
+        a, b, c = (dev(v, dt) for v in (S.a, S.b, S.c))
+        d = dev(dpad.reshape(-1), dt)
+        x = torch.full((nrhs * ldx,), 7.0, dtype=dt, device="cuda")
+        tdp.tdp_solve_multi(a, b, c, d, x, n, nrhs, ldd, ldx, s, code)
+        torch.cuda.synchronize()
+        X = host(x).reshape(nrhs, ldx)
+        assert (X[:, n:] == 7.0).all(), (n, nrhs, s)
+        for j in range(nrhs):
+            ref = oracle.thomas(S.a, S.b, S.c, D[j])
+            e = oracle.rel_err(X[j, :n], ref)
+            assert e <= TOL[code], (n, nrhs, s, j, e)

@@ -41,6 +41,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 STREAM_A, STREAM_B, STREAM_C, STREAM_X, STREAM_N, STREAM_G1, STREAM_G2, STREAM_U = range(8)
+STREAM_RHS = 16  # right-hand-side columns use streams 16, 17, ...
 
 
 def mix64(z: np.ndarray) -> np.ndarray:
@@ -171,3 +172,9 @@ def heat(n: int = 2048, r: float = 0.5, seed: int = 0) -> Heat:
     b = np.full((n, n), 1.0 + 2.0 * r)
     c = np.full((n, n), -r)
     return Heat(n, r, u, a, b, c)
+
+
+def rhs_columns(n: int, nrhs: int, seed: int = 0) -> np.ndarray:
+    """nrhs right-hand sides of n rows for one matrix, each U[-1, 1]
+    (column j from stream 16 + j); shape (nrhs, n)."""
+    return np.stack([uniform(seed, STREAM_RHS + j, n, -1.0, 1.0) for j in range(nrhs)])
