@@ -175,3 +175,33 @@ def test_many_rhs_2e22x16(tdp):
     X = x.cpu().numpy().reshape(nrhs, n)
     for j in range(nrhs):
         assert oracle.rel_err(X[j], oracle.thomas(S.a, S.b, S.c, D[j])) <= 1e-12, j
+
+
+@pytest.mark.parametrize("code", [0, 2])
+def test_single_system_2e28_largest_swept(tdp, code):
+    """The largest size of the size-model sweeps, 2^28 unknowns (2 GiB per
+    binary64 array): every element against the oracle, so that no index of
+    the kernels or the interface levels overflows at the top of the range."""
+    import os
+
+    import torch
+
+    n = 1 << 28
+    free, _ = torch.cuda.mem_get_info()
+    try:
+        host_bytes = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        host_bytes = 0
+    if free < 40 * (1 << 30) or host_bytes < 48 * (1 << 30):
+        pytest.skip("needs 40 GiB of free device memory and 48 GiB of host memory")
+    S = W.single(n, seed=5)
+    ref = oracle.thomas(S.a, S.b, S.c, S.d)
+    a, b, c, d = (_dev(getattr(S, k), torch.float64) for k in "abcd")
+    del S
+    x = torch.empty_like(d)
+    tdp.tdp_solve(a, b, c, d, x, n, 0, code, 1 if code == 2 else 0)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy()
+    del a, b, c, d, x
+    torch.cuda.empty_cache()
+    assert oracle.rel_err(got, ref) <= TOL[code]
