@@ -249,6 +249,8 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_COOP_REG 16    /* 1: the one-launch interface tail reads its 8-row blocks into registers */
 #define TDP_TUNE_BATCH_FLAT 17  /* 1: tdp_solve_batched with at least 4096 rows per system on average solves the
                                    batch as one block-diagonal system on the single-system tiles */
+#define TDP_TUNE_VTILE_B 18     /* 1: binary64 Stage 1 at s = 8 or 16 keeps b in registers and a, c, d in the
+                                   interleaved tile (a quarter less shared memory per row) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

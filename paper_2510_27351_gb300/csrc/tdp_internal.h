@@ -68,6 +68,7 @@ struct Ctx {
   bool events_ok = true;       // the profiler may create CUDA events around launches
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
+  bool vtile_b = true;         // binary64 Stage 1 at s = 8, 16 with b in registers (TDP_VTILE_B=0 off)
   bool coop = true;            // small interface levels in one cooperative launch (TDP_COOP=0 off)
   int s_tail = 8;              // sub-system size inside that launch (TDP_S_TAIL)
   bool fused_refine = false;   // one fused pass per refinement correction (TDP_FUSED_REFINE=1)

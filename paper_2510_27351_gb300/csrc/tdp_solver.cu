@@ -14,6 +14,7 @@
 #include "tdp_internal.h"
 #include "tdp_tma.cuh"
 #include "tdp_vtile.cuh"
+#include "tdp_vtile_b.cuh"
 #include "tdp_coop.cuh"
 #include "tdp_wtile.cuh"
 #include "tdp_refine.cuh"
@@ -286,6 +287,20 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
         post_launch(ctx, "stage 1");
         return;
       }
+    }
+  }
+  if constexpr (!MAPPED && KEEP && std::is_same<S, double>::value && std::is_same<C, double>::value) {
+    if (ctx.vtile && ctx.vtile_b && (s == 8 || s == 16)) {
+      // b in registers, a, c, d in the tile (tdp_vtile_b.cuh)
+      const int T = s == 8 ? 128 : 64;
+      const size_t smem = size_t(3) * 8 * s * (T + 1);
+      auto vk = s == 8 ? k_stage1_vb<8> : k_stage1_vb<16>;
+      allow_smem(vk);
+      pre_launch(ctx, nm);
+      vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, m, ra, rb, rc, rd, ka, kg, kd,
+                                                             ctx.flat_off, ctx.flat_nsys, ctx.status);
+      post_launch(ctx, "stage 1");
+      return;
     }
   }
   if constexpr (!MAPPED && std::is_same<S, C>::value) {

@@ -53,7 +53,7 @@ def _solve(tdp, S, s, code, iters=1):
 
 
 SIZES = [1, 2, 3, 4, 5, 31, 32, 33, 63, 64, 65, 1000, 4097, 65536, 100_003]
-SUBS = [2, 3, 4, 7, 8, 32, 64, 100, 1024]
+SUBS = [2, 3, 4, 7, 8, 16, 32, 64, 100, 1024]
 
 
 @pytest.mark.parametrize("code", [0, 1, 2])
@@ -480,7 +480,8 @@ def test_refinement_last_pass_variants(tdp, kept):
         tdp.tdp_set_tuning(tdp.TUNE_REFINE_KEPT, old)
 
 
-@pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 0)])
+@pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 0),
+                                       ("TUNE_VTILE_B", 0)])
 def test_tuning_variants(tdp, key, value):
     """Non-default kernel choices give the same answers: register-staged
     tiles instead of the interleaved cp.async tiles, the one-launch tail
