@@ -49,12 +49,13 @@ void allow_smem(K kernel) {
 
 // Threads (= blocks) per CTA for a tile kernel holding `arrays` tiles of
 // `elem` bytes per row, plus 4 bytes per row of owner table when mapped.
-int pick_threads(const Ctx& ctx, int s, int arrays, int elem, bool mapped, size_t* smem_out) {
+int pick_threads(const Ctx& ctx, int s, int arrays, int elem, bool mapped, size_t* smem_out, int budget = 0) {
   auto bytes = [&](int T) {
     return size_t(arrays) * elem * size_t(s) * (T + 1) + (mapped ? size_t(4) * T * s : 0);
   };
+  const size_t limit = size_t(budget > 0 ? std::min(budget, ctx.smem_budget) : ctx.smem_budget);
   int T = 256;
-  while (T > 32 && bytes(T) > size_t(ctx.smem_budget)) T /= 2;
+  while (T > 32 && bytes(T) > limit) T /= 2;
   while (T > 1 && bytes(T) > size_t(kMaxSmem)) --T;
   *smem_out = bytes(T);
   return T;
@@ -306,7 +307,9 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
   if constexpr (!MAPPED && std::is_same<S, C>::value) {
     if (ctx.vtile && s % Vec<S>::W == 0) {
       size_t smem;
-      const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
+      // binary32 tiles: smaller CTAs (at most 64 KB) interleave their load
+      // and sweep phases better (N = 2^26, s = 64: 0.797 -> 0.765 ms)
+      const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
       auto vk = k_stage1_v<S, C, KEEP>;
       allow_smem(vk);
       pre_launch(ctx, nm);
@@ -382,7 +385,7 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
   }
   if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
     size_t smem;
-    const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem);
+    const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
     auto vk = k_stage3_resolve_v<S, C>;
     allow_smem(vk);
     pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
