@@ -573,3 +573,60 @@ def test_many_rhs_vs_oracle(tdp, code):
             ref = oracle.thomas(S.a, S.b, S.c, D[j])
             e = oracle.rel_err(X[j, :n], ref)
             assert e <= TOL[code], (n, nrhs, s, j, e)
+
+
+def test_randomised_configurations(tdp):
+    """Seeded random mix of sizes, sub-system sizes, precisions and entry
+    points (single, batched with and without the one-system form, many
+    right-hand sides), every answer against the oracle."""
+    import random
+
+    import torch
+
+    rng = random.Random(2024)
+    for case in range(60):
+        code = rng.choice([0, 1, 2])
+        dt = torch.float32 if code == 1 else torch.float64
+        it = rng.choice([1, 2]) if code == 2 else 0
+        kind = rng.choice(["single", "batched", "multi"]) if code != 2 else rng.choice(["single", "batched"])
+        s = rng.choice([0, 2, 3, 4, 5, 8, 12, 16, 20, 24, 32, 48, 64, 100])
+        if kind == "single":
+            n = int(round(2 ** rng.uniform(0, 17)))
+            S = W.single(n, seed=case)
+            x = _solve(tdp, S, s, code, it)
+            assert oracle.rel_err(x, oracle.thomas(S.a, S.b, S.c, S.d)) <= TOL[code], (case, n, s, code)
+        elif kind == "batched":
+            sizes = [int(round(2 ** rng.uniform(0, 14))) for _ in range(rng.randint(1, 40))]
+            if rng.random() < 0.3:
+                sizes[rng.randrange(len(sizes))] = 0
+            Sb = W.batched(sizes=sizes, seed=case)
+            if Sb.n == 0:
+                continue
+            ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+            a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(dev(Sb.offsets), len(sizes), Sb.n, a, b, c, d, x, s, code, it)
+            torch.cuda.synchronize()
+            got = host(x)
+            for j in range(len(sizes)):
+                lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
+                if hi > lo:
+                    assert oracle.rel_err(got[lo:hi], ref[lo:hi]) <= TOL[code], (case, sizes, s, code, j)
+        else:
+            n = int(round(2 ** rng.uniform(0, 15)))
+            nrhs = rng.randint(1, 12)
+            v = 4 if code == 1 else 2
+            ld = -(-n // v) * v
+            S = W.single(n, seed=case)
+            D = W.rhs_columns(n, nrhs, seed=case)
+            dpad = np.zeros((nrhs, ld))
+            dpad[:, :n] = D
+            a, b, c = (dev(vv, dt) for vv in (S.a, S.b, S.c))
+            d = dev(dpad.reshape(-1), dt)
+            x = torch.zeros_like(d)  # the padding past n stays as it is
+            tdp.tdp_solve_multi(a, b, c, d, x, n, nrhs, ld, ld, s, code)
+            torch.cuda.synchronize()
+            X = host(x).reshape(nrhs, ld)
+            for j in range(nrhs):
+                ref = oracle.thomas(S.a, S.b, S.c, D[j])
+                assert oracle.rel_err(X[j, :n], ref) <= TOL[code], (case, n, nrhs, s, code, j)
