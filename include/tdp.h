@@ -109,6 +109,20 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
                     int64_t sys_stride, int64_t elem_stride, int32_t s, tdp_dtype dtype, int32_t refine_iters,
                     void* stream);
 
+/* tdp_solve with HOST arrays (a, b, c, d in, x out; n elements each), for
+ * callers whose data are not on the device yet.  Pinned host memory
+ * (cudaHostAlloc / cudaHostRegister) lets the copies overlap the solve: the
+ * binary64 and binary32 solves run in about eight chunks, Stage 1 of a chunk
+ * while the next one is copied in, Stage 3 of a chunk while the previous one is
+ * copied out (a second stream that the call creates and releases); the answer
+ * is the one tdp_solve gives, bit for bit.  The refinement copies everything
+ * in, solves and copies out.  Asynchronous on `stream` like tdp_solve: x is
+ * complete when the stream's work is.  The device copies of the arrays live
+ * in the workspace (5n elements).  Other arguments and errors as tdp_solve;
+ * x must not overlap an input. */
+int tdp_solve_host(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
+                   tdp_dtype dtype, int32_t refine_iters, void* stream);
+
 /* Many right-hand sides with one matrix (not in the paper): solve A X = D for
  * nrhs columns of n unknowns.  Column j of D starts at element j*ldd of d, column
  * j of X at element j*ldx of x (ldd, ldx >= n; the X and D ranges must not

@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_recursion_plan.argtypes = [I64, I32, I32, I32, P, I32]
     lib.tdp_recursion_plan.restype = I32
     lib.tdp_solve_multi.argtypes = [P, P, P, P, P, I64, I32, I64, I64, I32, I32, P]
+    lib.tdp_solve_host.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
     return lib
 
 
@@ -81,7 +82,7 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
-           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi")
+           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi", "tdp_solve_host")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
  TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S,
@@ -177,6 +178,17 @@ def tdp_load_table(path: str):
 def tdp_solve_const(a, b, c, d, x, n, batch, sys_stride, elem_stride, s, dtype, refine_iters=0, stream=None):
     _check(LIB.tdp_solve_const(float(a), float(b), float(c), _ptr(d), _ptr(x), int(n), int(batch), int(sys_stride),
                                int(elem_stride), int(s), int(dtype), int(refine_iters), _stream(stream)))
+
+
+def tdp_solve_host(a, b, c, d, x, n, s=0, dtype=F64, refine_iters=0, stream=None):
+    """tdp_solve on CPU tensors (pinned memory lets the copies overlap the solve)."""
+    for t in (a, b, c, d, x):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("tdp_solve_host takes contiguous host tensors")
+    _check(LIB.tdp_solve_host(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                              ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(d.data_ptr()),
+                              ctypes.c_void_p(x.data_ptr()), int(n), int(s), int(dtype), int(refine_iters),
+                              _stream(stream)))
 
 
 def tdp_solve_multi(a, b, c, d, x, n, nrhs, ldd, ldx, s=0, dtype=F64, stream=None):

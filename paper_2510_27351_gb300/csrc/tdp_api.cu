@@ -512,6 +512,22 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
   });
 }
 
+int tdp_solve_host(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
+                   tdp_dtype dtype, int32_t refine_iters, void* stream) {
+  const char* fn = "tdp_solve_host";
+  int rc = check_common(n, s, dtype, refine_iters, fn);
+  if (rc) return rc;
+  if (!a || !b || !c || !d || !x) return set_error(TDP_EINVAL, std::string(fn) + ": null pointer");
+  const size_t el = dtype == TDP_F32 ? 4 : 8;
+  const uintptr_t x0 = reinterpret_cast<uintptr_t>(x), x1 = x0 + size_t(n) * el;
+  for (const void* p : {a, b, c, d}) {
+    const uintptr_t p0 = reinterpret_cast<uintptr_t>(p), p1 = p0 + size_t(n) * el;
+    if (x0 < p1 && p0 < x1) return set_error(TDP_EINVAL, std::string(fn) + ": x overlaps an input");
+  }
+  const int ss = s ? s : predict_s(n, 1, dtype);
+  return run(stream, fn, [&](Ctx& ctx) { solve_host(ctx, a, b, c, d, x, n, ss, dtype, refine_iters); });
+}
+
 int tdp_solve_multi(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t nrhs,
                     int64_t ldd, int64_t ldx, int32_t s, tdp_dtype dtype, void* stream) {
   const char* fn = "tdp_solve_multi";

@@ -60,6 +60,7 @@ struct Ctx {
   bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
   bool coop_reg = true;              // one-launch tail: 8-row blocks through registers (TDP_COOP_REG)
   bool batch_flat = true;            // batches of large systems as one block-diagonal system (TDP_BATCH_FLAT)
+  int64_t kb = 0, ke = -1;           // system-level Stage 1/3 launches cover blocks [kb, ke) (-1: all)
   const int64_t* flat_off = nullptr; // set while such a batch is solved: its offsets (device)
   int32_t flat_nsys = 0;             // and number of systems
   const int64_t* seg_bbase = nullptr;  // the batch whose interface system is being solved: blocks
@@ -117,6 +118,8 @@ int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);
 int32_t predict_r(int64_t n, int32_t batch, tdp_dtype dt);
 int load_rtable_file(const char* path);
 int recursion_plan(int64_t n, int32_t batch, int32_t s, int R, tdp_dtype dt, int32_t* m_out, int cap);
+void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
+                tdp_dtype dt, int refine_iters);
 void solve_multi(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
                  int32_t nrhs, int64_t ldd, int64_t ldx, int s, tdp_dtype dt);
 // Flattened table for the device-side predictor: rows of (log2 n, log2 batch, s) per dtype.

@@ -325,12 +325,13 @@ template <typename C, typename S, bool MAPPED>
 __global__ void __launch_bounds__(256) k_stage3_kept(const C* __restrict__ ka, const C* __restrict__ kg,
                                                      const C* __restrict__ kd, int64_t n, int s, unsigned magic,
                                                      int64_t m, const int64_t* __restrict__ blk,
-                                                     const double* __restrict__ y, S* __restrict__ x) {
+                                                     const double* __restrict__ y, S* __restrict__ x, int64_t kb,
+                                                     int64_t ke) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x;
-  const int64_t k0 = int64_t(blockIdx.x) * T;
-  if (k0 >= m) return;
-  const int nb = int(min(int64_t(T), m - k0));
+  const int64_t k0 = kb + int64_t(blockIdx.x) * T;  // blocks [kb, ke) of the m
+  if (k0 >= ke) return;
+  const int nb = int(min(int64_t(T), ke - k0));
   C* yl = reinterpret_cast<C*>(smem);
   C* yr = yl + T;
   uint32_t* own = reinterpret_cast<uint32_t*>(yr + T);

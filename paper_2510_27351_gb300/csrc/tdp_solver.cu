@@ -10,6 +10,7 @@
 #include <tuple>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 #include "tdp_internal.h"
 #include "tdp_tma.cuh"
@@ -297,9 +298,10 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       const size_t smem = size_t(3) * 8 * s * (T + 1);
       auto vk = s == 8 ? k_stage1_vb<8> : k_stage1_vb<16>;
       allow_smem(vk);
+      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
       pre_launch(ctx, nm);
-      vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, m, ra, rb, rc, rd, ka, kg, kd,
-                                                             ctx.flat_off, ctx.flat_nsys, ctx.status);
+      vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, m, ra, rb, rc, rd, ka, kg, kd,
+                                                                   ctx.flat_off, ctx.flat_nsys, kb, ke, ctx.status);
       post_launch(ctx, "stage 1");
       return;
     }
@@ -312,9 +314,10 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
       auto vk = k_stage1_v<S, C, KEEP>;
       allow_smem(vk);
+      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
       pre_launch(ctx, nm);
-      vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
-                                                             ctx.flat_off, ctx.flat_nsys, ctx.status);
+      vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
+                                                                   ctx.flat_off, ctx.flat_nsys, kb, ke, ctx.status);
       post_launch(ctx, "stage 1");
       return;
     }
@@ -361,9 +364,10 @@ void stage3_kept(Ctx& ctx, const C* ka, const C* kg, const C* kd, int64_t n, int
   const size_t need = size_t(2) * T * sizeof(C) + (MAPPED ? size_t(4) * T * s : 0);
   auto kern = k_stage3_kept<C, S, MAPPED>;
   allow_smem(kern);
-  const int64_t grid = (m + T - 1) / T;
+  const int64_t kb = MAPPED ? 0 : ctx.kb, ke = (!MAPPED && ctx.ke >= 0) ? ctx.ke : m;
   pre_launch(ctx, name ? name : "stage3_kept_f64");
-  kern<<<unsigned(grid), T, need, ctx.stream>>>(ka, kg, kd, n, s, magic_for(s), m, blk, y, x);
+  kern<<<unsigned((ke - kb + T - 1) / T), T, need, ctx.stream>>>(ka, kg, kd, n, s, magic_for(s), m, blk, y, x, kb,
+                                                                 ke);
   post_launch(ctx, "stage 3");
 }
 
@@ -388,9 +392,10 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
     const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
     auto vk = k_stage3_resolve_v<S, C>;
     allow_smem(vk);
+    const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
     pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
-    vk<<<unsigned((m + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.flat_off, ctx.flat_nsys,
-                                                           ctx.status);
+    vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.flat_off,
+                                                                 ctx.flat_nsys, kb, ke, ctx.status);
     post_launch(ctx, "stage 3");
     return;
   }
@@ -555,14 +560,19 @@ bool solve_interface_seg(Ctx& ctx, const double* ra, const double* rb, const dou
 void solve_interface(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
                      int64_t M) {
   if (M <= 0) return;
-  // the interface system has no system boundaries to cut
+  // the interface system has no system boundaries to cut and is solved whole
   const int64_t* flat_off = ctx.flat_off;
   const int32_t flat_nsys = ctx.flat_nsys;
+  const int64_t kb = ctx.kb, ke = ctx.ke;
   ctx.flat_off = nullptr;
   ctx.flat_nsys = 0;
+  ctx.kb = 0;
+  ctx.ke = -1;
   if (!solve_interface_seg(ctx, ra, rb, rc, rd, y, M)) solve_interface_levels(ctx, ra, rb, rc, rd, y, M);
   ctx.flat_off = flat_off;
   ctx.flat_nsys = flat_nsys;
+  ctx.kb = kb;
+  ctx.ke = ke;
 }
 
 void solve_interface_levels(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
@@ -1382,6 +1392,129 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
     post_launch(ctx, "cut edges");
   }
   solve_blocks<false>(ctx, a2, b, c2, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);
+}
+
+// ---------------------------------------------------------------------------
+// Host arrays in, host array out.  The binary64 and binary32 solves are
+// pipelined over about eight chunks of whole tiles: while chunk k+1 is being
+// copied in (a second stream), Stage 1 runs on chunk k; after the interface
+// solve, chunk k's Stage 3 runs while chunk k-1 is copied out.  Tiles and
+// arithmetic are those of the one-piece solve, so the answer is the same bit
+// for bit.  Other schedules copy everything in, solve, and copy out.
+// ---------------------------------------------------------------------------
+void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
+                tdp_dtype dt, int refine_iters) {
+  ctx.rec_n = n;
+  ctx.rec_batch = 1;
+  ctx.rec_dt = dt;
+  if (s > n) s = int(std::max<int64_t>(2, n));
+  const size_t el = dt == TDP_F32 ? 4 : 8;
+  char* ad = ctx.ar->take<char>(size_t(n) * el);
+  char* bd = ctx.ar->take<char>(size_t(n) * el);
+  char* cd = ctx.ar->take<char>(size_t(n) * el);
+  char* dd = ctx.ar->take<char>(size_t(n) * el);
+  char* xd = ctx.ar->take<char>(size_t(n) * el);
+  const char* hsrc[4] = {(const char*)a, (const char*)b, (const char*)c, (const char*)d};
+  char* dsrc[4] = {ad, bd, cd, dd};
+  const bool chunked = ctx.vtile && !ctx.tma && !ctx.pipeline &&
+                       (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0 && !ctx.wtile));
+  if (!chunked) {
+    if (!ctx.dry && ctx.err == cudaSuccess)
+      for (int i = 0; i < 4; ++i)
+        ctx.fail(cudaMemcpyAsync(dsrc[i], hsrc[i], size_t(n) * el, cudaMemcpyHostToDevice, ctx.stream), "copy in");
+    solve_single(ctx, ad, bd, cd, dd, xd, n, s, dt, refine_iters);
+    if (!ctx.dry && ctx.err == cudaSuccess)
+      ctx.fail(cudaMemcpyAsync(x, xd, size_t(n) * el, cudaMemcpyDeviceToHost, ctx.stream), "copy out");
+    return;
+  }
+  const int64_t m = (n + s - 1) / s;
+  const int64_t ch = std::max<int64_t>(256, ((m + 7) / 8 + 255) / 256 * 256);  // blocks per chunk, whole tiles
+  const int64_t nch = (m + ch - 1) / ch;
+  Iface32Scope f32(ctx, dt != TDP_F64);
+  double* ra = ctx.ar->take<double>(2 * m);
+  double* rb = ctx.ar->take<double>(2 * m);
+  double* rc = ctx.ar->take<double>(2 * m);
+  double* rd = ctx.ar->take<double>(2 * m);
+  double* y = ctx.ar->take<double>(2 * m);
+  double* ka = dt == TDP_F64 ? ctx.ar->take<double>(n) : nullptr;
+  double* kg = dt == TDP_F64 ? ctx.ar->take<double>(n) : nullptr;
+  double* kd = dt == TDP_F64 ? ctx.ar->take<double>(n) : nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto event = [&]() {
+    cudaEvent_t e = nullptr;
+    ctx.fail(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    if (e) evs.push_back(e);
+    return e;
+  };
+  const bool live = !ctx.dry && ctx.err == cudaSuccess;
+  if (live) ctx.fail(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "copy stream");
+  auto rows = [&](int64_t k, int64_t& r0, int64_t& r1) {
+    r0 = k * ch * s;
+    r1 = std::min<int64_t>(n, (k + 1) * ch * s);
+  };
+  // copy in and Stage 1, chunk by chunk
+  for (int64_t k = 0; k < nch; ++k) {
+    int64_t r0, r1;
+    rows(k, r0, r1);
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      cudaEvent_t ready = event();
+      if (ctx.err == cudaSuccess && k == 0) {  // the copies start after the caller's earlier work
+        cudaEvent_t go = event();
+        ctx.fail(cudaEventRecord(go, ctx.stream), "event");
+        ctx.fail(cudaStreamWaitEvent(cs, go, 0), "event");
+      }
+      for (int i = 0; i < 4 && ctx.err == cudaSuccess; ++i)
+        ctx.fail(cudaMemcpyAsync(dsrc[i] + r0 * el, hsrc[i] + r0 * el, size_t(r1 - r0) * el,
+                                 cudaMemcpyHostToDevice, cs), "copy in");
+      if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(ready, cs), "event");
+      if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(ctx.stream, ready, 0), "event");
+    }
+    ctx.kb = k * ch;
+    ctx.ke = std::min(m, (k + 1) * ch);
+    if (dt == TDP_F64)
+      stage1<double, double, false, true>(ctx, (const double*)ad, (const double*)bd, (const double*)cd,
+                                          (const double*)dd, n, s, m, nullptr, ra, rb, rc, rd, ka, kg, kd);
+    else
+      stage1<float, float, false, false>(ctx, (const float*)ad, (const float*)bd, (const float*)cd,
+                                         (const float*)dd, n, s, m, nullptr, ra, rb, rc, rd, (float*)nullptr,
+                                         (float*)nullptr, (float*)nullptr);
+  }
+  ctx.kb = 0;
+  ctx.ke = -1;
+  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
+  // Stage 3 and copy out, chunk by chunk
+  for (int64_t k = 0; k < nch; ++k) {
+    int64_t r0, r1;
+    rows(k, r0, r1);
+    ctx.kb = k * ch;
+    ctx.ke = std::min(m, (k + 1) * ch);
+    if (dt == TDP_F64)
+      stage3_kept<double, double, false>(ctx, ka, kg, kd, n, s, m, nullptr, y, (double*)xd);
+    else
+      stage3_resolve<float, float, false>(ctx, (const float*)ad, (const float*)bd, (const float*)cd,
+                                          (const float*)dd, n, s, m, nullptr, y, (float*)xd);
+    if (!ctx.dry && ctx.err == cudaSuccess) {
+      cudaEvent_t done = event();
+      if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(done, ctx.stream), "event");
+      if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(cs, done, 0), "event");
+      if (ctx.err == cudaSuccess)
+        ctx.fail(cudaMemcpyAsync((char*)x + r0 * el, xd + r0 * el, size_t(r1 - r0) * el, cudaMemcpyDeviceToHost,
+                                 cs), "copy out");
+    }
+  }
+  ctx.kb = 0;
+  ctx.ke = -1;
+  if (cs) {
+    // the caller's stream waits for the last copy out
+    if (ctx.err == cudaSuccess) {
+      cudaEvent_t fin = event();
+      if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(fin, cs), "event");
+      if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(ctx.stream, fin, 0), "event");
+    }
+    cudaStreamDestroy(cs);  // released once its work is done
+  }
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,

@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(256) k_stage1_v(const S* __restrict__ a, const
                                                   int64_t m, double* __restrict__ ra, double* __restrict__ rb,
                                                   double* __restrict__ rc, double* __restrict__ rd,
                                                   C* __restrict__ ka, C* __restrict__ kg, C* __restrict__ kd,
-                                                  const int64_t* __restrict__ off, int32_t nsys,
-                                                  unsigned* __restrict__ status) {
+                                                  const int64_t* __restrict__ off, int32_t nsys, int64_t kb,
+                                                  int64_t ke, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x, ldv = T + 1;
-  const int64_t k0 = int64_t(blockIdx.x) * T;
-  if (k0 >= m) return;
-  const int nb = int(min(int64_t(T), m - k0));
+  const int64_t k0 = kb + int64_t(blockIdx.x) * T;  // blocks [kb, ke) of the m
+  if (k0 >= ke) return;
+  const int nb = int(min(int64_t(T), ke - k0));
   const size_t plane = size_t(s) * ldv;
   S* A = reinterpret_cast<S*>(smem);
   S* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};
@@ -309,12 +309,13 @@ __global__ void __launch_bounds__(256) k_stage3_resolve_v(const S* __restrict__ 
                                                           const S* __restrict__ c, const S* __restrict__ d,
                                                           int64_t n, int s, int64_t m, const double* __restrict__ y,
                                                           S* __restrict__ x, const int64_t* __restrict__ off,
-                                                          int32_t nsys, unsigned* __restrict__ status) {
+                                                          int32_t nsys, int64_t kb, int64_t ke,
+                                                          unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x, ldv = T + 1;
-  const int64_t k0 = int64_t(blockIdx.x) * T;
-  if (k0 >= m) return;
-  const int nb = int(min(int64_t(T), m - k0));
+  const int64_t k0 = kb + int64_t(blockIdx.x) * T;  // blocks [kb, ke) of the m
+  if (k0 >= ke) return;
+  const int nb = int(min(int64_t(T), ke - k0));
   const size_t plane = size_t(s) * ldv;
   S* A = reinterpret_cast<S*>(smem);
   S* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};

@@ -19,15 +19,15 @@ __global__ void __launch_bounds__(256) k_stage1_vb(const double* __restrict__ a,
                                                    double* __restrict__ rb, double* __restrict__ rc,
                                                    double* __restrict__ rd, double* __restrict__ ka,
                                                    double* __restrict__ kg, double* __restrict__ kd,
-                                                   const int64_t* __restrict__ off, int32_t nsys,
-                                                   unsigned* __restrict__ status) {
+                                                   const int64_t* __restrict__ off, int32_t nsys, int64_t kb,
+                                                   int64_t ke, unsigned* __restrict__ status) {
   static_assert(SB % 2 == 0 && SB >= 4, "even block size of at least 4");
   constexpr int V = 2, G = SB / V;
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x, t = threadIdx.x, ldv = T + 1;
-  const int64_t k0 = int64_t(blockIdx.x) * T;
-  if (k0 >= m) return;
-  const int nb = int(min(int64_t(T), m - k0));
+  const int64_t k0 = kb + int64_t(blockIdx.x) * T;  // blocks [kb, ke) of the m
+  if (k0 >= ke) return;
+  const int nb = int(min(int64_t(T), ke - k0));
   const size_t plane = size_t(SB) * ldv;
   double* A = reinterpret_cast<double*>(smem);
   double* Cc = A + plane;

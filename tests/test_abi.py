@@ -71,6 +71,13 @@ def test_bad_arguments_rejected_on_host():
     assert "aligned" in tdp.tdp_last_error()
     assert m(16, 16, 16, 1 << 20, 1 << 24, 11, 2, 11, 12, 4, 0, 0) == 1     # odd column stride
     assert "16-byte" in tdp.tdp_last_error()
+    # host arrays: (a, b, c, d, x, n, s, dtype, refine_iters, stream)
+    h = lib.tdp_solve_host
+    assert h(16, 16, 16, 0, 1 << 24, 10, 4, 0, 0, 0) == 1
+    assert "null" in tdp.tdp_last_error()
+    assert h(16, 16, 16, 1 << 20, (1 << 20) + 8, 10, 4, 0, 0, 0) == 1
+    assert "overlaps" in tdp.tdp_last_error()
+    assert h(16, 16, 16, 1 << 20, 1 << 24, 0, 4, 0, 0, 0) == 1
 
 
 def test_predictor_is_host_only_and_valid():

@@ -630,3 +630,32 @@ def test_randomised_configurations(tdp):
             for j in range(nrhs):
                 ref = oracle.thomas(S.a, S.b, S.c, D[j])
                 assert oracle.rel_err(X[j, :n], ref) <= TOL[code], (case, n, nrhs, s, code, j)
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
+def test_solve_host_arrays(tdp, code):
+    """tdp_solve_host: host arrays in and out (pinned and pageable), the
+    chunked copy/compute pipeline giving exactly tdp_solve's answer, and the
+    oracle's within tolerance."""
+    import torch
+
+    dt = torch.float32 if code == 1 else torch.float64
+    it = 1 if code == 2 else 0
+    for n, s in ((1, 0), (1000, 8), (100_003, 16), (100_003, 12), ((1 << 22) + 777, 0), ((1 << 22) + 5, 64)):
+        S = W.single(n, seed=n)
+        ref = oracle.thomas(S.a, S.b, S.c, S.d)
+        for pinned in (True, False):
+            hs = [torch.from_numpy(getattr(S, k)).to(dt) for k in "abcd"]
+            if pinned:
+                hs = [h.pin_memory() for h in hs]
+            hx = torch.empty_like(hs[0])
+            if pinned:
+                hx = hx.pin_memory()
+            tdp.tdp_solve_host(*hs, hx, n, s, code, it)
+            torch.cuda.synchronize()
+            got = hx.double().numpy()
+            assert oracle.rel_err(got, ref) <= TOL[code], (n, s, code, pinned)
+            dev_x = torch.empty(n, dtype=dt, device="cuda")
+            tdp.tdp_solve(*[h.cuda() for h in hs], dev_x, n, s, code, it)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(dev_x), got), (n, s, code, pinned)
