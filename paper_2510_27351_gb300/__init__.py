@@ -86,7 +86,7 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
  TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S,
- TUNE_IFACE32, TUNE_REFINE_KEPT, TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B) = range(19)
+ TUNE_IFACE32, TUNE_REFINE_KEPT, TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B, TUNE_VTILE_L) = range(20)
 
 
 def _check(rc: int):

@@ -82,14 +82,15 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // from kept binary32 coefficients), TDP_COOP_REG (1: the one-launch tail
 // reads its 8-row blocks into registers), TDP_BATCH_FLAT (1: batches of
 // systems of at least 4096 rows on average are solved as one block-diagonal
-// system) and TDP_VTILE_B (1: binary64 Stage 1 at s = 8 or 16 keeps b in
-// registers and a, c, d in the tile).
+// system), TDP_VTILE_B (1: binary64 Stage 1 at s = 8 or 16 keeps b in
+// registers and a, c, d in the tile) and TDP_VTILE_L (1: binary32 storage
+// runs the full blocks of Stage 1 and Stage 3 on padded block-major tiles).
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
 };
-Knob g_knobs[19] = {
+Knob g_knobs[20] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
     {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
     {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
@@ -99,7 +100,7 @@ Knob g_knobs[19] = {
     {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
     {"TDP_IFACE32", 0, 1, {1}},                            {"TDP_REFINE_KEPT", 0, 1, {1}},
     {"TDP_COOP_REG", 0, 1, {1}},                           {"TDP_BATCH_FLAT", 0, 1, {1}},
-    {"TDP_VTILE_B", 0, 1, {1}},
+    {"TDP_VTILE_B", 0, 1, {1}},                            {"TDP_VTILE_L", 0, 2, {1}},
 };
 std::once_flag g_knobs_once;
 
@@ -135,6 +136,7 @@ void tune_from_env(Ctx& ctx) {
   ctx.coop_reg = g_knobs[TDP_TUNE_COOP_REG].v.load() != 0;
   ctx.batch_flat = g_knobs[TDP_TUNE_BATCH_FLAT].v.load() != 0;
   ctx.vtile_b = g_knobs[TDP_TUNE_VTILE_B].v.load() != 0;
+  ctx.vtile_l = g_knobs[TDP_TUNE_VTILE_L].v.load();
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

@@ -16,6 +16,7 @@
 #include "tdp_tma.cuh"
 #include "tdp_vtile.cuh"
 #include "tdp_vtile_b.cuh"
+#include "tdp_vtile_l.cuh"
 #include "tdp_coop.cuh"
 #include "tdp_wtile.cuh"
 #include "tdp_refine.cuh"
@@ -269,6 +270,19 @@ WCfg wtile_cfg(K kern, int s, int64_t m) {
   return c;
 }
 
+// Padded block-major binary32 tiles (tdp_vtile_l.cuh): threads per CTA (=
+// blocks per tile) with at most 64 KB of tile per CTA, as for the
+// interleaved binary32 tiles, fewer than 32 only where a block's rows need
+// it (s up to 1024: 16 KB per thread).
+int ltile_threads(int s, size_t* smem) {
+  const size_t per = size_t(4) * size_t(ltile_pitch(s / 4)) * 16;  // four planes of pv 16-byte chunks
+  int T = 256;
+  while (T > 32 && per * T > size_t(64) * 1024) T /= 2;
+  while (T > 1 && per * T + 16 > size_t(kMaxSmem)) --T;
+  *smem = per * T + 16;  // and the mbarrier of the bulk copies
+  return T;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -289,6 +303,26 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
         post_launch(ctx, "stage 1");
         return;
       }
+    }
+  }
+  int64_t kb_v = ctx.kb;  // first block of the interleaved tiles below
+  if constexpr (!MAPPED && !KEEP && std::is_same<S, float>::value && std::is_same<C, float>::value) {
+    if (ctx.vtile && ctx.vtile_l > 0 && s % 4 == 0) {
+      // full blocks on the padded block-major tiles (tdp_vtile_l.cuh), a ragged last block below
+      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
+      const int64_t kf = std::max(kb, std::min(ke, n / s));
+      if (kf > kb) {
+        size_t smem;
+        const int T = ltile_threads(s, &smem);
+        auto lk = ctx.vtile_l == 2 ? k_stage1_l<true> : k_stage1_l<false>;
+        allow_smem(lk);
+        pre_launch(ctx, nm);
+        lk<<<unsigned((kf - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, s, m, ra, rb, rc, rd, ctx.flat_off,
+                                                                     ctx.flat_nsys, kb, kf, ctx.status);
+        post_launch(ctx, "stage 1");
+      }
+      if (kf == ke) return;
+      kb_v = kf;
     }
   }
   if constexpr (!MAPPED && KEEP && std::is_same<S, double>::value && std::is_same<C, double>::value) {
@@ -314,7 +348,7 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
       auto vk = k_stage1_v<S, C, KEEP>;
       allow_smem(vk);
-      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
+      const int64_t kb = kb_v, ke = ctx.ke >= 0 ? ctx.ke : m;
       pre_launch(ctx, nm);
       vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
                                                                    ctx.flat_off, ctx.flat_nsys, kb, ke, ctx.status);
@@ -387,12 +421,31 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
       }
     }
   }
+  int64_t kb_v = ctx.kb;  // first block of the interleaved tiles below
+  if constexpr (!MAPPED && std::is_same<S, float>::value && std::is_same<C, float>::value) {
+    if (ctx.vtile && ctx.vtile_l > 0 && s % 4 == 0) {
+      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
+      const int64_t kf = std::max(kb, std::min(ke, n / s));
+      if (kf > kb) {
+        size_t smem;
+        const int T = ltile_threads(s, &smem);
+        auto lk = ctx.vtile_l == 2 ? k_stage3_resolve_l<true> : k_stage3_resolve_l<false>;
+        allow_smem(lk);
+        pre_launch(ctx, "stage3_resolve_f32");
+        lk<<<unsigned((kf - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, s, y, x, ctx.flat_off, ctx.flat_nsys,
+                                                                     kb, kf, ctx.status);
+        post_launch(ctx, "stage 3");
+      }
+      if (kf == ke) return;
+      kb_v = kf;
+    }
+  }
   if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
     size_t smem;
     const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
     auto vk = k_stage3_resolve_v<S, C>;
     allow_smem(vk);
-    const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
+    const int64_t kb = kb_v, ke = ctx.ke >= 0 ? ctx.ke : m;
     pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
     vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.flat_off,
                                                                  ctx.flat_nsys, kb, ke, ctx.status);

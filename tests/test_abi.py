@@ -132,7 +132,7 @@ def test_tuning_knobs_validate_and_round_trip():
             assert tdp.tdp_get_tuning(key) in (0, 1) and tdp.tdp_get_tuning(key) == v, key
         with pytest.raises(tdp.TdpError):
             tdp.tdp_set_tuning(tdp.TUNE_IFACE32, 2)
-        assert tdp.tdp_get_tuning(tdp.TUNE_VTILE_B + 1) == -1
+        assert tdp.tdp_get_tuning(tdp.TUNE_VTILE_L + 1) == -1
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_S_REC, old)
 

@@ -481,12 +481,13 @@ def test_refinement_last_pass_variants(tdp, kept):
 
 
 @pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 0),
-                                       ("TUNE_VTILE_B", 0)])
+                                       ("TUNE_VTILE_B", 0), ("TUNE_VTILE_L", 0)])
 def test_tuning_variants(tdp, key, value):
     """Non-default kernel choices give the same answers: register-staged
     tiles instead of the interleaved cp.async tiles, the one-launch tail
-    without register-resident blocks, every interface level in binary64.
-    Sizes reach the interface levels above 2^19 rows."""
+    without register-resident blocks, every interface level in binary64,
+    binary32 full blocks on the interleaved tiles.  Sizes reach the
+    interface levels above 2^19 rows."""
     k = getattr(tdp, key)
     old = tdp.tdp_get_tuning(k)
     tdp.tdp_set_tuning(k, value)
@@ -542,6 +543,44 @@ def test_batched_as_one_system(tdp, code):
                     assert e <= TOL[code], (flat, s, it, j, e)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_BATCH_FLAT, old)
+
+
+def test_padded_binary32_tiles_match_interleaved_tiles(tdp):
+    """Binary32 storage: the full blocks of Stage 1 and Stage 3 on padded
+    block-major tiles, filled by 16-byte cp.async copies (TUNE_VTILE_L = 1)
+    or by one bulk copy per block and array (2), run the sweeps of the
+    interleaved tiles (TUNE_VTILE_L = 0), so the answers agree bit for bit:
+    single systems with and without a ragged last block, sub-systems up to
+    1024 rows (fewer than 32 blocks per tile), and a batch solved as one
+    system (cuts inside the tiles)."""
+    import torch
+
+    old = tdp.tdp_get_tuning(tdp.TUNE_VTILE_L)
+    cases = [W.single(n, seed=n) for n in (1, 5, 1000, 4096, 100_003, 1 << 20, (1 << 22) + 37)]
+    Sb = W.batched(sizes=[5000, 1, 0, 8193, 4096, 12000, 2, 7, 9999, 3, 6500], seed=11)
+    try:
+        for S in cases + [Sb]:
+            a, b, c, d = (dev(v, torch.float32) for v in (S.a, S.b, S.c, S.d))
+            batched = S is Sb
+            off = dev(Sb.offsets) if batched else None
+            for s in (4, 24, 64, 100, 1024):
+                got = {}
+                for v in (0, 1, 2):
+                    tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, v)
+                    x = torch.full_like(d, float("nan"))
+                    if batched:
+                        tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, s, 1, 0)
+                    else:
+                        tdp.tdp_solve(a, b, c, d, x, S.n, s, 1, 0)
+                    torch.cuda.synchronize()
+                    got[v] = host(x)
+                for v in (1, 2):
+                    assert np.array_equal(got[v], got[0]), (S.n, s, v)
+                ref = (oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets) if batched
+                       else oracle.thomas(S.a, S.b, S.c, S.d))
+                assert oracle.rel_err(got[1], ref) <= TOL[1], (S.n, s)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, old)
 
 
 @pytest.mark.parametrize("code", [0, 1])
