@@ -265,8 +265,8 @@ int64_t tdp_launch_count(void);
                                    batch as one block-diagonal system on the single-system tiles */
 #define TDP_TUNE_VTILE_B 18     /* 1: binary64 Stage 1 at s = 8 or 16 keeps b in registers and a, c, d in the
                                    interleaved tile (a quarter less shared memory per row) */
-#define TDP_TUNE_VTILE_L 19     /* 1: binary32 storage runs Stage 1 and Stage 3 of full blocks on padded
-                                   block-major tiles (each block's rows contiguous in shared memory) */
+#define TDP_TUNE_VTILE_L 19     /* 1: binary32 storage runs Stage 1 and Stage 3 on padded block-major tiles
+                                   (each block's rows contiguous in shared memory) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

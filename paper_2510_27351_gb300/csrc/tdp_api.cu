@@ -84,7 +84,7 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // systems of at least 4096 rows on average are solved as one block-diagonal
 // system), TDP_VTILE_B (1: binary64 Stage 1 at s = 8 or 16 keeps b in
 // registers and a, c, d in the tile) and TDP_VTILE_L (1: binary32 storage
-// runs the full blocks of Stage 1 and Stage 3 on padded block-major tiles).
+// runs Stage 1 and Stage 3 on padded block-major tiles).
 struct Knob {
   const char* env;
   int lo, hi;
@@ -100,7 +100,7 @@ Knob g_knobs[20] = {
     {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
     {"TDP_IFACE32", 0, 1, {1}},                            {"TDP_REFINE_KEPT", 0, 1, {1}},
     {"TDP_COOP_REG", 0, 1, {1}},                           {"TDP_BATCH_FLAT", 0, 1, {1}},
-    {"TDP_VTILE_B", 0, 1, {1}},                            {"TDP_VTILE_L", 0, 2, {1}},
+    {"TDP_VTILE_B", 0, 1, {1}},                            {"TDP_VTILE_L", 0, 1, {1}},
 };
 std::once_flag g_knobs_once;
 
@@ -136,7 +136,7 @@ void tune_from_env(Ctx& ctx) {
   ctx.coop_reg = g_knobs[TDP_TUNE_COOP_REG].v.load() != 0;
   ctx.batch_flat = g_knobs[TDP_TUNE_BATCH_FLAT].v.load() != 0;
   ctx.vtile_b = g_knobs[TDP_TUNE_VTILE_B].v.load() != 0;
-  ctx.vtile_l = g_knobs[TDP_TUNE_VTILE_L].v.load();
+  ctx.vtile_l = g_knobs[TDP_TUNE_VTILE_L].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

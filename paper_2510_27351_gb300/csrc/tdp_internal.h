@@ -70,7 +70,7 @@ struct Ctx {
   bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
   bool vtile_b = true;         // binary64 Stage 1 at s = 8, 16 with b in registers (TDP_VTILE_B=0 off)
-  int vtile_l = 1;             // binary32 storage: full blocks on padded block-major tiles (0 off, 2 bulk copies)
+  bool vtile_l = true;         // binary32 storage: padded block-major tiles (TDP_VTILE_L=0 off)
   bool coop = true;            // small interface levels in one cooperative launch (TDP_COOP=0 off)
   int s_tail = 8;              // sub-system size inside that launch (TDP_S_TAIL)
   bool fused_refine = false;   // one fused pass per refinement correction (TDP_FUSED_REFINE=1)

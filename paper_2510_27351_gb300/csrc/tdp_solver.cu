@@ -278,8 +278,8 @@ int ltile_threads(int s, size_t* smem) {
   const size_t per = size_t(4) * size_t(ltile_pitch(s / 4)) * 16;  // four planes of pv 16-byte chunks
   int T = 256;
   while (T > 32 && per * T > size_t(64) * 1024) T /= 2;
-  while (T > 1 && per * T + 16 > size_t(kMaxSmem)) --T;
-  *smem = per * T + 16;  // and the mbarrier of the bulk copies
+  while (T > 1 && per * T > size_t(kMaxSmem)) --T;
+  *smem = per * T;
   return T;
 }
 
@@ -305,24 +305,19 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       }
     }
   }
-  int64_t kb_v = ctx.kb;  // first block of the interleaved tiles below
   if constexpr (!MAPPED && !KEEP && std::is_same<S, float>::value && std::is_same<C, float>::value) {
-    if (ctx.vtile && ctx.vtile_l > 0 && s % 4 == 0) {
-      // full blocks on the padded block-major tiles (tdp_vtile_l.cuh), a ragged last block below
+    if (ctx.vtile && ctx.vtile_l && s % 4 == 0) {
+      // padded block-major tiles (tdp_vtile_l.cuh)
       const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
-      const int64_t kf = std::max(kb, std::min(ke, n / s));
-      if (kf > kb) {
-        size_t smem;
-        const int T = ltile_threads(s, &smem);
-        auto lk = ctx.vtile_l == 2 ? k_stage1_l<true> : k_stage1_l<false>;
-        allow_smem(lk);
-        pre_launch(ctx, nm);
-        lk<<<unsigned((kf - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, s, m, ra, rb, rc, rd, ctx.flat_off,
-                                                                     ctx.flat_nsys, kb, kf, ctx.status);
-        post_launch(ctx, "stage 1");
-      }
-      if (kf == ke) return;
-      kb_v = kf;
+      size_t smem;
+      const int T = ltile_threads(s, &smem);
+      allow_smem(k_stage1_l);
+      pre_launch(ctx, nm);
+      k_stage1_l<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd,
+                                                                           ctx.flat_off, ctx.flat_nsys, kb, ke,
+                                                                           ctx.status);
+      post_launch(ctx, "stage 1");
+      return;
     }
   }
   if constexpr (!MAPPED && KEEP && std::is_same<S, double>::value && std::is_same<C, double>::value) {
@@ -348,7 +343,7 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
       auto vk = k_stage1_v<S, C, KEEP>;
       allow_smem(vk);
-      const int64_t kb = kb_v, ke = ctx.ke >= 0 ? ctx.ke : m;
+      const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
       pre_launch(ctx, nm);
       vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ka, kg, kd,
                                                                    ctx.flat_off, ctx.flat_nsys, kb, ke, ctx.status);
@@ -421,23 +416,17 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
       }
     }
   }
-  int64_t kb_v = ctx.kb;  // first block of the interleaved tiles below
   if constexpr (!MAPPED && std::is_same<S, float>::value && std::is_same<C, float>::value) {
-    if (ctx.vtile && ctx.vtile_l > 0 && s % 4 == 0) {
+    if (ctx.vtile && ctx.vtile_l && s % 4 == 0) {
       const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
-      const int64_t kf = std::max(kb, std::min(ke, n / s));
-      if (kf > kb) {
-        size_t smem;
-        const int T = ltile_threads(s, &smem);
-        auto lk = ctx.vtile_l == 2 ? k_stage3_resolve_l<true> : k_stage3_resolve_l<false>;
-        allow_smem(lk);
-        pre_launch(ctx, "stage3_resolve_f32");
-        lk<<<unsigned((kf - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, s, y, x, ctx.flat_off, ctx.flat_nsys,
-                                                                     kb, kf, ctx.status);
-        post_launch(ctx, "stage 3");
-      }
-      if (kf == ke) return;
-      kb_v = kf;
+      size_t smem;
+      const int T = ltile_threads(s, &smem);
+      allow_smem(k_stage3_resolve_l);
+      pre_launch(ctx, "stage3_resolve_f32");
+      k_stage3_resolve_l<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(
+          a, b, c, d, n, s, m, y, x, ctx.flat_off, ctx.flat_nsys, kb, ke, ctx.status);
+      post_launch(ctx, "stage 3");
+      return;
     }
   }
   if (!MAPPED && ctx.vtile && std::is_same<S, C>::value && s % Vec<S>::W == 0) {
@@ -445,7 +434,7 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
     const int T = pick_threads(ctx, s, 4, sizeof(S), false, &smem, sizeof(S) == 4 ? 64 * 1024 : 0);
     auto vk = k_stage3_resolve_v<S, C>;
     allow_smem(vk);
-    const int64_t kb = kb_v, ke = ctx.ke >= 0 ? ctx.ke : m;
+    const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
     pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
     vk<<<unsigned((ke - kb + T - 1) / T), T, smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.flat_off,
                                                                  ctx.flat_nsys, kb, ke, ctx.status);

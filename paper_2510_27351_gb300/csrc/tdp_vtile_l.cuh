@@ -1,5 +1,5 @@
 // Padded block-major tiles for binary32 storage: Stage 1 without kept
-// coefficients and Stage 3 by the interior solve, for full blocks.
+// coefficients and Stage 3 by the interior solve.
 //
 // The interleaved tiles (tdp_vtile.cuh) put chunk g (16 bytes, V rows) of
 // block t at word g (T + 1) + t, so the 16-byte cp.async copies of one warp,
@@ -8,18 +8,11 @@
 // (its s / V chunks and one or two chunks of padding, pv odd), chunk g at
 // word t pv + g: the copies of a warp land in one or two contiguous runs.
 // The sweeps read chunk g of thread t at word t pv + g; pv odd puts the
-// eight threads of every quarter warp on eight different bank groups.
-// Blocks must be full (len = s): the host sends a ragged last block to the
-// interleaved kernels.  Arithmetic as in k_stage1_v / k_stage3_resolve_v
-// (the same lean sweeps), so the results agree bit for bit.
-//
-// BULK: instead of 16-byte cp.async copies, thread t issues one 1-D bulk
-// copy (cp.async.bulk, the TMA engine) per array of its own block's s rows
-// into its padded run; the copies complete on one mbarrier (bounded wait:
-// after about a second the CTA raises ST_TIMEOUT, waits once more for its
-// copies and skips its blocks).
+// eight threads of every quarter warp on eight different bank groups.  Full
+// blocks take the lean sweeps, a ragged last block the per-row sweeps with
+// unit stride (its rows are contiguous); the arithmetic is that of
+// k_stage1_v / k_stage3_resolve_v, so the results agree bit for bit.
 #pragma once
-#include "tdp_tma.cuh"
 #include "tdp_vtile.cuh"
 
 namespace tdp {
@@ -27,19 +20,27 @@ namespace tdp {
 // Chunks of the padded run of one block: s / V plus one or two, odd.
 __host__ __device__ __forceinline__ int ltile_pitch(int cps) { return cps + ((cps & 1) ? 2 : 1); }
 
-// Copies of the nb full blocks of the tile starting at row ts into the
-// padded layout, four arrays.
+// Copies of four arrays, rows [ts, te) of whole blocks, into the padded
+// layout; chunks that reach past n are read element by element (zero fill).
 template <typename S>
-__device__ __forceinline__ void ltile_issue(int64_t ts, int nb, int s, int pv, const S* const (&src)[4],
-                                            S* const (&pl)[4]) {
+__device__ __forceinline__ void ltile_issue(int64_t ts, int64_t te, int64_t n, int s, int pv,
+                                            const S* const (&src)[4], S* const (&pl)[4]) {
   constexpr int V = Vec<S>::W;
-  const int cps = s / V, chunks = nb * cps;
+  const int chunks = int((te - ts + V - 1) / V);
+  const int cps = s / V;
   for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
     const int t = q / cps, g = q - t * cps;
     const int64_t row = ts + int64_t(q) * V;
     const int idx = (t * pv + g) * V;
+    if (row + V <= n) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) cp_async16(pl[i] + idx, src[i] + row);
+      for (int i = 0; i < 4; ++i) cp_async16(pl[i] + idx, src[i] + row);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int u = 0; u < V; ++u) pl[i][idx + u] = (row + u < n) ? src[i][row + u] : S(0);
+    }
   }
 }
 
@@ -62,57 +63,28 @@ __device__ __forceinline__ void ltile_cut(int64_t ts, int64_t te, int s, int pv,
   }
 }
 
-// Load, and cut for a batch solved as one system, the tile of blocks
-// [k0, k0 + nb) (rows from ts = k0 s).  False when a bulk copy wait ran out.
-// BULK: `bar` is an 8-byte mbarrier in shared memory.
-template <typename S, bool BULK>
-__device__ __forceinline__ bool ltile_load(const S* a, const S* b, const S* c, const S* d, int64_t k0, int nb, int s,
-                                           int pv, const int64_t* off, int32_t nsys, S* const (&pl)[4], uint64_t* bar,
-                                           unsigned* status) {
-  constexpr int V = Vec<S>::W;
-  const int64_t ts = k0 * s, te = ts + int64_t(nb) * s;
+// Load, and cut for a batch solved as one system, the tile of rows [ts, te).
+template <typename S>
+__device__ __forceinline__ void ltile_load(const S* a, const S* b, const S* c, const S* d, int64_t ts, int64_t te,
+                                           int64_t n, int s, int pv, const int64_t* off, int32_t nsys,
+                                           S* const (&pl)[4]) {
   const S* const src[4] = {a, b, c, d};
-  const int t = threadIdx.x;
-  if constexpr (BULK) {
-    if (t == 0) {
-      mbar_init(bar, 1);
-      mbar_init_fence();
-    }
-    __syncthreads();
-    const unsigned bytes = unsigned(s) * unsigned(sizeof(S));
-    if (t == 0) mbar_expect_tx(bar, 4u * unsigned(nb) * bytes);
-    if (t < nb) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) bulk_g2s(pl[i] + t * pv * V, src[i] + ts + int64_t(t) * s, bytes, bar);
-    }
-  } else {
-    ltile_issue<S>(ts, nb, s, pv, src, pl);
-  }
+  ltile_issue<S>(ts, te, n, s, pv, src, pl);
   int jb = 0;
-  if (off && t < 32) jb = warp_lower_bound(off, 1, nsys, ts);  // while the copies fly
-  if constexpr (BULK) {
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, status));
-    if (!ok) {
-      mbar_wait_bounded(bar, 0, nullptr);  // one more bounded wait for the copies in flight
-      return false;
-    }
-  } else {
-    cp_async_commit_wait_all();
-    __syncthreads();
-  }
+  if (off && threadIdx.x < 32) jb = warp_lower_bound(off, 1, nsys, ts);  // while the copies fly
+  cp_async_commit_wait_all();
+  __syncthreads();
   if (off) {
-    if (t < 32) ltile_cut<S>(ts, te, s, pv, off, nsys, jb, pl[0], pl[2]);
+    if (threadIdx.x < 32) ltile_cut<S>(ts, te, s, pv, off, nsys, jb, pl[0], pl[2]);
     __syncthreads();
   }
-  return true;
 }
 
-// Stage 1 (interface rows only) of the full blocks [kb, ke), T per CTA.
-// Shared memory: four planes of T pv V elements (and the mbarrier).
-template <bool BULK>
+// Stage 1 (interface rows only) of the blocks [kb, ke), T per CTA.  Shared
+// memory: four planes of T pv V elements.
 __global__ void __launch_bounds__(256) k_stage1_l(const float* __restrict__ a, const float* __restrict__ b,
-                                                  const float* __restrict__ c, const float* __restrict__ d, int s,
-                                                  int64_t m, double* __restrict__ ra, double* __restrict__ rb,
+                                                  const float* __restrict__ c, const float* __restrict__ d, int64_t n,
+                                                  int s, int64_t m, double* __restrict__ ra, double* __restrict__ rb,
                                                   double* __restrict__ rc, double* __restrict__ rd,
                                                   const int64_t* __restrict__ off, int32_t nsys, int64_t kb,
                                                   int64_t ke, unsigned* __restrict__ status) {
@@ -126,27 +98,31 @@ __global__ void __launch_bounds__(256) k_stage1_l(const float* __restrict__ a, c
   const size_t plane = size_t(T) * pv * V;
   float* A = reinterpret_cast<float*>(smem);
   float* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};
-  if (!ltile_load<float, BULK>(a, b, c, d, k0, nb, s, pv, off, nsys, pl, reinterpret_cast<uint64_t*>(A + 4 * plane),
-                               status))
-    return;
+  const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
+  ltile_load<float>(a, b, c, d, ts, te, n, s, pv, off, nsys, pl);
   if (t < nb) {
-    const int64_t k = k0 + t;
+    const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
     const int o = t * pv * V;
-    float z = 0.0f;
-    const IfaceRows r = wreduce_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, k == 0, k == m - 1, z);
-    if (!(z == 0.0f)) flag(status, ST_SINGULAR);
-    write_iface(k, r, ra, rb, rc, rd);
+    IfaceRows r;
+    if (bi.len == s) {
+      float z = 0.0f;
+      r = wreduce_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, bi.first, bi.last, z);
+      if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+    } else {
+      r = block_reduce<float, float, false>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, 1, bi, status);
+    }
+    write_iface(k0 + t, r, ra, rb, rc, rd);
   }
 }
 
-// Stage 3 by the interior solve of the full blocks [kb, ke), x from the
-// interface values y; same tiles as k_stage1_l.
-template <bool BULK>
+// Stage 3 by the interior solve of the blocks [kb, ke), x from the interface
+// values y; same tiles as k_stage1_l.
 __global__ void __launch_bounds__(256) k_stage3_resolve_l(const float* __restrict__ a, const float* __restrict__ b,
                                                           const float* __restrict__ c, const float* __restrict__ d,
-                                                          int s, const double* __restrict__ y, float* __restrict__ x,
-                                                          const int64_t* __restrict__ off, int32_t nsys, int64_t kb,
-                                                          int64_t ke, unsigned* __restrict__ status) {
+                                                          int64_t n, int s, int64_t m, const double* __restrict__ y,
+                                                          float* __restrict__ x, const int64_t* __restrict__ off,
+                                                          int32_t nsys, int64_t kb, int64_t ke,
+                                                          unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int V = 4;
   const int T = blockDim.x, t = threadIdx.x;
@@ -159,21 +135,31 @@ __global__ void __launch_bounds__(256) k_stage3_resolve_l(const float* __restric
   float* const pl[4] = {A, A + plane, A + 2 * plane, A + 3 * plane};
   double2 yv = make_double2(0.0, 0.0);
   if (t < nb) yv = *reinterpret_cast<const double2*>(y + 2 * (k0 + t));
-  const int64_t ts = k0 * s;
-  if (!ltile_load<float, BULK>(a, b, c, d, k0, nb, s, pv, off, nsys, pl, reinterpret_cast<uint64_t*>(A + 4 * plane),
-                               status))
-    return;
+  const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
+  ltile_load<float>(a, b, c, d, ts, te, n, s, pv, off, nsys, pl);
   if (t < nb) {
+    const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
     const int o = t * pv * V;
-    float z = 0.0f;
-    wsubstitute_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, yv.x, yv.y, z);
-    if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+    if (bi.len == s) {
+      float z = 0.0f;
+      wsubstitute_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, yv.x, yv.y, z);
+      if (!(z == 0.0f)) flag(status, ST_SINGULAR);
+    } else {
+      block_substitute<float, float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, 1, bi.len, cvt<float>(yv.x),
+                                     cvt<float>(yv.y), status);
+    }
   }
   __syncthreads();
-  const int chunks = nb * cps;
+  const int chunks = int((te - ts + V - 1) / V);
   for (int q = t; q < chunks; q += T) {
     const int tt = q / cps, g = q - tt * cps;
-    stg16<float>(x + ts + int64_t(q) * V, lds16<float>(pl[3] + (tt * pv + g) * V));
+    const int64_t row = ts + int64_t(q) * V;
+    const float* p = pl[3] + (tt * pv + g) * V;
+    if (row + V <= te) {
+      stg16<float>(x + row, lds16<float>(p));
+    } else {
+      for (int u = 0; u < V && row + u < te; ++u) x[row + u] = p[u];
+    }
   }
 }
 
