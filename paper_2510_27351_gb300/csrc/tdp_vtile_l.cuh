@@ -28,6 +28,15 @@ __device__ __forceinline__ void ltile_issue(int64_t ts, int64_t te, int64_t n, i
   constexpr int V = Vec<S>::W;
   const int chunks = int((te - ts + V - 1) / V);
   const int cps = s / V;
+  if (ts + int64_t(chunks) * V <= n) {  // the whole tile inside the arrays (every tile but the last)
+    for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+      const int t = q / cps, g = q - t * cps;
+      const int idx = (t * pv + g) * V;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cp_async16(pl[i] + idx, src[i] + ts + int64_t(q) * V);
+    }
+    return;
+  }
   for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
     const int t = q / cps, g = q - t * cps;
     const int64_t row = ts + int64_t(q) * V;
@@ -101,17 +110,18 @@ __global__ void __launch_bounds__(256) k_stage1_l(const float* __restrict__ a, c
   const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
   ltile_load<float>(a, b, c, d, ts, te, n, s, pv, off, nsys, pl);
   if (t < nb) {
-    const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
+    const int64_t k = k0 + t;
     const int o = t * pv * V;
     IfaceRows r;
-    if (bi.len == s) {
+    if ((k + 1) * s <= n) {  // full block
       float z = 0.0f;
-      r = wreduce_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, bi.first, bi.last, z);
+      r = wreduce_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, k == 0, k == m - 1, z);
       if (!(z == 0.0f)) flag(status, ST_SINGULAR);
     } else {
+      const BlockInfo bi = block_info<false>(k, n, s, m, nullptr);
       r = block_reduce<float, float, false>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, 1, bi, status);
     }
-    write_iface(k0 + t, r, ra, rb, rc, rd);
+    write_iface(k, r, ra, rb, rc, rd);
   }
 }
 
@@ -138,19 +148,26 @@ __global__ void __launch_bounds__(256) k_stage3_resolve_l(const float* __restric
   const int64_t ts = k0 * s, te = min(n, (k0 + nb) * s);
   ltile_load<float>(a, b, c, d, ts, te, n, s, pv, off, nsys, pl);
   if (t < nb) {
-    const BlockInfo bi = block_info<false>(k0 + t, n, s, m, nullptr);
+    const int64_t k = k0 + t;
     const int o = t * pv * V;
-    if (bi.len == s) {
+    if ((k + 1) * s <= n) {  // full block
       float z = 0.0f;
       wsubstitute_full<float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, s, V, yv.x, yv.y, z);
       if (!(z == 0.0f)) flag(status, ST_SINGULAR);
     } else {
-      block_substitute<float, float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, 1, bi.len, cvt<float>(yv.x),
-                                     cvt<float>(yv.y), status);
+      block_substitute<float, float>(pl[0] + o, pl[1] + o, pl[2] + o, pl[3] + o, 1, int(n - k * s),
+                                     cvt<float>(yv.x), cvt<float>(yv.y), status);
     }
   }
   __syncthreads();
   const int chunks = int((te - ts + V - 1) / V);
+  if (te == (k0 + nb) * s) {  // whole blocks only: 16-byte stores throughout
+    for (int q = t; q < chunks; q += T) {
+      const int tt = q / cps, g = q - tt * cps;
+      stg16<float>(x + ts + int64_t(q) * V, lds16<float>(pl[3] + (tt * pv + g) * V));
+    }
+    return;
+  }
   for (int q = t; q < chunks; q += T) {
     const int tt = q / cps, g = q - tt * cps;
     const int64_t row = ts + int64_t(q) * V;
