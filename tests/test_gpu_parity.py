@@ -335,6 +335,45 @@ def test_warp_bulk_tiles(tdp, code):
         tdp.tdp_set_tuning(tdp.TUNE_WTILE, old)
 
 
+@pytest.mark.parametrize("knobs", [("TUNE_TMA",), ("TUNE_PIPELINE",), ("TUNE_FUSED_REFINE",),
+                                   ("TUNE_FUSED_REFINE", "TUNE_PIPELINE")])
+def test_opt_in_tile_variants(tdp, knobs):
+    """The opt-in tile variants kept for measurement (CTA-wide bulk copies
+    with a transpose pass, per-warp element-copy pipelines, the fused
+    refinement passes) against the oracle, with the interleaved tiles off so
+    that every tile kernel takes them: ragged last blocks, an array end inside
+    a 16-byte chunk, several tiles per CTA, and a batch with the block map."""
+    keys = [getattr(tdp, k) for k in knobs] + [tdp.TUNE_VTILE]
+    old = [tdp.tdp_get_tuning(k) for k in keys]
+    for k in keys[:-1]:
+        tdp.tdp_set_tuning(k, 1)
+    tdp.tdp_set_tuning(tdp.TUNE_VTILE, 0)
+    codes = (2,) if "TUNE_FUSED_REFINE" in knobs else (0, 1, 2)
+    try:
+        for n in (5, 63, 1000, 4097, 100_003, 1 << 20):
+            S = W.single(n, seed=n + 3)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for code in codes:
+                for s in (3, 8, 24, 64):
+                    e = oracle.rel_err(_solve(tdp, S, s, code), ref)
+                    assert e <= TOL[code], (knobs, n, code, s, e)
+        import torch
+
+        Sb = W.batched(64, 2, 3000, seed=5)
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        off = dev(Sb.offsets)
+        for code in codes:
+            dt = torch.float32 if code == 1 else torch.float64
+            a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+            x = torch.empty_like(d)
+            tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, 8, code, 1 if code == 2 else 0)
+            torch.cuda.synchronize()
+            assert oracle.rel_err(host(x), ref) <= TOL[code], (knobs, code)
+    finally:
+        for k, v in zip(keys, old):
+            tdp.tdp_set_tuning(k, v)
+
+
 @pytest.mark.parametrize("code", [0, 1, 2])
 def test_paper_recursion_schedule(tdp, code):
     """The recursive variant (Sec. III) with R forced to 0..5 and predicted:
