@@ -533,7 +533,8 @@ int tdp_solve_host(const void* a, const void* b, const void* c, const void* d, v
 int tdp_solve_multi(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t nrhs,
                     int64_t ldd, int64_t ldx, int32_t s, tdp_dtype dtype, void* stream) {
   const char* fn = "tdp_solve_multi";
-  if (dtype != TDP_F64 && dtype != TDP_F32) return set_error(TDP_EINVAL, std::string(fn) + ": dtype must be F64 or F32");
+  if (dtype != TDP_F64 && dtype != TDP_F32)
+    return set_error(TDP_EINVAL, std::string(fn) + ": dtype must be F64 or F32");
   int rc = check_common(n, s, dtype, 0, fn);
   if (rc) return rc;
   if (nrhs < 1 || nrhs > 65535) return set_error(TDP_EINVAL, std::string(fn) + ": nrhs must be in [1, 65535]");
@@ -541,7 +542,8 @@ int tdp_solve_multi(const void* a, const void* b, const void* c, const void* d, 
   if (!a || !b || !c || !d || !x) return set_error(TDP_EINVAL, std::string(fn) + ": null pointer");
   const size_t el = dtype == TDP_F32 ? 4 : 8;
   for (const void* p : {a, b, c, d, (const void*)x})
-    if (reinterpret_cast<uintptr_t>(p) % 16) return set_error(TDP_EINVAL, std::string(fn) + ": pointer not 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(p) % 16)
+      return set_error(TDP_EINVAL, std::string(fn) + ": pointer not 16-byte aligned");
   if ((size_t(ldd) * el) % 16 || (size_t(ldx) * el) % 16)
     return set_error(TDP_EINVAL, std::string(fn) + ": columns must start on 16-byte boundaries (ldd, ldx)");
   const uintptr_t x0 = reinterpret_cast<uintptr_t>(x), d0 = reinterpret_cast<uintptr_t>(d);

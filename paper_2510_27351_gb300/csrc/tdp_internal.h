@@ -55,7 +55,7 @@ struct Ctx {
   tdp_dtype rec_dt = TDP_F64;
   bool seg = true;                   // per-system interface solves for batches (TDP_SEGMENTED=0 off)
   bool per_system_s = false;         // batched s = 0: one s per system from the device model (TDP_PER_SYSTEM_S=1)
-  bool iface32 = true;               // binary32 arithmetic in the first interface level of binary32 solves (TDP_IFACE32)
+  bool iface32 = true;               // binary32 arithmetic in the first interface level of binary32 solves
   bool iface32_on = false;           // set while such a solve runs
   bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
   bool coop_reg = true;              // one-launch tail: 8-row blocks through registers (TDP_COOP_REG)
