@@ -37,6 +37,7 @@ import workloads as W  # noqa: E402
 
 N_MAIN = 1 << 26
 METRIC = "unknowns solved/sec (FP64 partition solve, N=2^26)"
+WORKLOAD = "single tridiagonal system N=2^26, binary64, b~U[4,8], a,c~U[-1,1], d=A x*"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # binary64 pipe: 2 FMA per clock per SM (the nominal 1.25 TFLOP/s over
 # 152 SMs at 2.07 GHz), 2 flops per FMA
@@ -211,7 +212,7 @@ def _reference_line(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "single tridiagonal system N=2^26, binary64", "n": N_MAIN, "batch": 1},
+        "config": {"workload": WORKLOAD, "n": N_MAIN, "batch": 1},
         "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -377,8 +378,7 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single tridiagonal system N=2^26, binary64, b~U[4,8], a,c~U[-1,1], d=A x*",
-                       "n": N_MAIN, "batch": 1, "s": s_main, "parallelism": f"replicas{world}",
+            "config": {"workload": WORKLOAD, "n": N_MAIN, "batch": 1, "s": s_main, "parallelism": f"replicas{world}",
                        "l2": "inputs (2 GiB) larger than L2; no flush"},
             "roofline": roof, "hbm_frac_of_whole_solve": solve_hbm_frac, "peaks_source": pk_src,
             "hbm_peak_gbs": hbm_peak, "kernels_ms": {k: v[1] for k, v in prof.items()},
