@@ -131,3 +131,23 @@ def test_precision_transfer_study_on_synthetic_sweeps():
     assert shifted["best_fixed_s"] == 32 and shifted["target_loo_mean_time_loss"] == 0.0
     assert set(rep) == {f"{a}->{b}/batch1" for a in ("f64", "f32", "f32_refine")
                         for b in ("f64", "f32", "f32_refine") if a != b}
+
+
+def test_committed_tables_are_derived_from_the_committed_sweeps(tmp_path):
+    """The size table compiled into the library (tdp_table.inc), its text copy
+    and the recursion-depth table are exactly what tune.py derives from the
+    committed GB300 sweeps: a re-sweep that was not turned into tables, or a
+    hand-edited table, fails here."""
+    from paper_2510_27351_gb300 import tune
+
+    pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2510_27351_gb300")
+    data = os.path.join(pkg, "data")
+    cases = [(tune.build_table, tune.write_table, "sweep_gb300.jsonl", "table_gb300.txt", "tdp_table.inc"),
+             (tune.build_rtable, tune.write_rtable, "sweep_r_gb300.jsonl", "table_r_gb300.txt", "tdp_rtable.inc")]
+    for build, write, sweep, txt, inc in cases:
+        out_txt, out_inc = str(tmp_path / txt), str(tmp_path / inc)
+        write(build(tune.load_sweep(os.path.join(data, sweep))), out_txt, out_inc)
+        with open(out_txt) as f1, open(os.path.join(data, txt)) as f2:
+            assert f1.read() == f2.read(), txt
+        with open(out_inc) as f1, open(os.path.join(pkg, "csrc", inc)) as f2:
+            assert f1.read() == f2.read(), inc
