@@ -151,3 +151,21 @@ def test_committed_tables_are_derived_from_the_committed_sweeps(tmp_path):
             assert f1.read() == f2.read(), txt
         with open(out_inc) as f1, open(os.path.join(pkg, "csrc", inc)) as f2:
             assert f1.read() == f2.read(), inc
+
+
+def test_committed_evaluations_are_reproduced_from_the_committed_sweeps():
+    """The evaluation reports quoted in the design notes (size model, recursion
+    depth model, transfer between precisions) are what tune.py computes from
+    the committed sweeps (fixed split seed)."""
+    import json
+
+    from paper_2510_27351_gb300 import tune
+
+    data = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2510_27351_gb300", "data")
+    rows = tune.load_sweep(os.path.join(data, "sweep_gb300.jsonl"))
+    rrows = tune.load_sweep(os.path.join(data, "sweep_r_gb300.jsonl"))
+    for got, name in ((tune.evaluate(rows), "evaluation_gb300.json"),
+                      (tune.evaluate_transfer(rows), "evaluation_transfer_gb300.json"),
+                      (tune.evaluate_r(rrows), "evaluation_r_gb300.json")):
+        with open(os.path.join(data, name)) as f:
+            assert json.loads(json.dumps(got)) == json.load(f), name
