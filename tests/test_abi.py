@@ -180,3 +180,27 @@ def test_recursion_depth_model_and_plan_match_the_oracle(tmp_path):
             for R in range(6):
                 assert tdp.tdp_recursion_plan(n, s, R) == P.recursive_sizes(n, s, R, pred), (n, s, R)
     assert tdp.LIB.tdp_recursion_plan(0, 8, 1, 0, 0, 0) == -1
+
+
+def test_builtin_predictor_matches_the_oracle_knn():
+    """tdp_predict_s with the built-in table is the oracle's 1-NN over the
+    same rows (log2 N and log2 batch features, ties to the larger s), query
+    by query: every table size, sizes between them, sizes outside the table,
+    batch sizes on and between the table's buckets."""
+    import paper_2510_27351_gb300 as tdp
+    from oracle import predictor as P
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rows = P.load_table(os.path.join(root, "paper_2510_27351_gb300", "data", "table_gb300.txt"))
+    for dt in (0, 1, 2):
+        mine = [(int(r[1]), int(r[2]), int(r[3])) for r in rows if int(r[0]) == dt]
+        assert mine, dt
+        ns = sorted({n for n, _, _ in mine})
+        queries = set(ns) | {1, 2, 100, 1 << 29, 3 << 28}
+        queries |= {int((x * y) ** 0.5) for x, y in zip(ns, ns[1:])}
+        queries |= {n + 1 for n in ns} | {n - 1 for n in ns}
+        for batch in (1, 2, 64, 100, 1024, 2000, 4096, 10000):
+            for n in sorted(queries):
+                want = P.knn_predict([r[0] for r in mine], [r[2] for r in mine], n, k=1,
+                                     train_batches=[r[1] for r in mine], query_batch=batch)
+                assert tdp.tdp_predict_s(n, batch, dt) == want, (dt, n, batch)
