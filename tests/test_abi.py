@@ -204,3 +204,20 @@ def test_builtin_predictor_matches_the_oracle_knn():
                 want = P.knn_predict([r[0] for r in mine], [r[2] for r in mine], n, k=1,
                                      train_batches=[r[1] for r in mine], query_batch=batch)
                 assert tdp.tdp_predict_s(n, batch, dt) == want, (dt, n, batch)
+
+
+def test_builtin_recursion_depth_model_matches_the_oracle_knn():
+    """tdp_predict_r with the built-in table is the oracle's 1-NN over the same
+    rows (R = -1 is the library's default schedule), query by query."""
+    import paper_2510_27351_gb300 as tdp
+    from oracle import predictor as P
+
+    rows = P.load_table(os.path.join(ROOT, "paper_2510_27351_gb300", "data", "table_r_gb300.txt"))
+    for dt in sorted({int(r[0]) for r in rows}):
+        mine = [(int(r[1]), int(r[2]), int(r[3])) for r in rows if int(r[0]) == dt]
+        ns = sorted({n for n, _, _ in mine})
+        queries = set(ns) | {1, 1000, 1 << 29} | {int((x * y) ** 0.5) for x, y in zip(ns, ns[1:])}
+        for n in sorted(queries):
+            want = P.knn_predict([r[0] for r in mine], [r[2] for r in mine], n, k=1,
+                                 train_batches=[r[1] for r in mine], query_batch=1)
+            assert tdp.tdp_predict_r(n, 1, dt) == want, (dt, n)
