@@ -39,12 +39,39 @@ N_MAIN = 1 << 26
 METRIC = "unknowns solved/sec (FP64 partition solve, N=2^26)"
 WORKLOAD = "single tridiagonal system N=2^26, binary64, b~U[4,8], a,c~U[-1,1], d=A x*"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# binary64 pipe: 2 FMA per clock per SM (the nominal 1.25 TFLOP/s over
-# 152 SMs at 2.07 GHz), 2 flops per FMA
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
-# algorithmic work per row of the binary64 Stage 1 (forward + backward sweep):
-# 8 FMA (pivot, 3 in the reciprocal, rhs, 3 backward) + 4 MUL -> 20 flops
-STAGE1_F64_FLOPS_PER_ROW = 20.0
+# binary64 pipe: 2 operations (FMA or MUL) per clock per SM, the nominal
+# 1.25 TFLOP/s over 152 SMs at 2.07 GHz with 2 flops per FMA
+FP64_PEAK_GOPS = 152 * 2.07e9 * 2 / 1e9
+FP64_PEAK_TFLOPS = FP64_PEAK_GOPS * 2 / 1e3
+
+
+def stage1_f64_ops(s):
+    """Binary64 FMAs and MULs of Stage 1 with kept coefficients per full block
+    of s rows: row 1 (reciprocal: 3 FMA; gamma, delta, alpha: 3 MUL), rows
+    2..s-1 (pivot, 3 in the reciprocal, delta: 5 FMA; q, gamma, d r, alpha:
+    4 MUL), the backward sweep over rows s-3..1 (ap, dp: 2 FMA; gp: 1 MUL)
+    and the top interface row (2 FMA, 1 MUL)."""
+    fma = 3 + 5 * (s - 2) + 2 * (s - 3) + 2
+    mul = 3 + 4 * (s - 2) + (s - 3) + 1
+    return fma, mul
+
+
+def stage1_f64_roofline(ms, n, s, hbm_peak_gbs, traffic=None):
+    """ALU roofline of the binary64 Stage 1 from its event-timed launch (ms):
+    binary64 pipe operations per second against the pipe's 2 per clock per
+    SM, and the same work in flops against the FMA-only flop peak."""
+    fma, mul = stage1_f64_ops(s)
+    ops = (fma + mul) * n / s
+    flops = (2 * fma + mul) * n / s
+    gops = ops / (ms * 1e-3) / 1e9
+    tflops = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": gops, "peak": FP64_PEAK_GOPS,
+            "unit": "Gop/s", "frac": gops / FP64_PEAK_GOPS, "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA or MUL per clock",
+            "ops_per_row": (fma + mul) / s, "fma_mul_per_block": [fma, mul],
+            "achieved_tflops": tflops, "peak_tflops": FP64_PEAK_TFLOPS, "frac_flops": tflops / FP64_PEAK_TFLOPS,
+            "algorithmic_bytes_per_row": 56 + 64 / s,
+            "hbm_frac_of_kernel": (56 + 64 / s) * n / (ms * 1e-3) / 1e9 / hbm_peak_gbs}
 
 
 def log(*a):
@@ -343,14 +370,8 @@ def run_ours(args, world, rank, local):
     st1 = prof.get("stage1_keep_f64")
     roof = None
     if st1:
-        flops = STAGE1_F64_FLOPS_PER_ROW * N_MAIN
-        ach = flops / (st1[1] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": measured_traffic("stage1_keep_f64", s_main, N_MAIN),
-                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA/clk x 2 flop",
-                "algorithmic_bytes_per_row": 56 + 64 / s_main,
-                "hbm_frac_of_kernel": (56 + 64 / s_main) * N_MAIN / (st1[1] * 1e-3) / 1e9 / hbm_peak}
+        roof = stage1_f64_roofline(st1[1], N_MAIN, s_main, hbm_peak,
+                                   measured_traffic("stage1_keep_f64", s_main, N_MAIN))
     solve_hbm_frac = value / world * 40 / 1e9 / hbm_peak
 
     # ---- end to end through the public API with host buffers ----
