@@ -224,6 +224,14 @@ int tdp_reserve(int64_t total_n, int32_t batch, int32_t s, tdp_dtype dtype, void
  * Returns TDP_OK, TDP_ESINGULAR, TDP_ETIMEOUT or TDP_EINVAL. */
 int tdp_status(void* stream);
 
+/* Return code that a device status word stands for (host only, no GPU
+ * needed): bit 4 (arguments rejected on the device) gives TDP_EINVAL, bit 2
+ * (a bounded wait ran out) TDP_ETIMEOUT, bit 1 (zero or non-finite pivot)
+ * TDP_ESINGULAR, in that order of precedence when several are set; 0 gives
+ * TDP_OK.  tdp_status, checked-mode solves and tdp_solve_noalloc all map
+ * the word this way. */
+int tdp_status_code(uint32_t bits);
+
 /* Checked mode: when on, every solve synchronises its stream and returns the
  * device status.  Default off. */
 void tdp_set_checked(int on);
@@ -244,10 +252,7 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_S_TAIL 2       /* sub-system size in the one-launch tail of that recursion [3, 256] */
 #define TDP_TUNE_VTILE 3        /* 1: 16-byte cp.async interleaved tiles for single systems */
 #define TDP_TUNE_COOP 4         /* 1: the small interface levels in one cooperative launch */
-#define TDP_TUNE_FUSED_REFINE 5 /* 1: one fused pass per refinement correction */
-#define TDP_TUNE_TMA 6          /* 1: TMA-staged tiles */
-#define TDP_TUNE_PIPELINE 7     /* 1: warp-tile cp.async pipeline (element copies) */
-#define TDP_TUNE_WTILE 8        /* 1: warp-owned bulk-copy (TMA) tiles for binary32 sweeps of single systems */
+/* keys 5 to 8 are retired (variants measured slower and removed); they are rejected */
 #define TDP_TUNE_REFINE3 9      /* 1: TDP_F32_REFINE runs its solve and first correction as three fused passes */
 #define TDP_TUNE_RECURSION 10   /* 1: the interface system follows the paper's recursion schedule (Sec. III);
                                    0: s = TDP_TUNE_S_REC levels down to 2^19 rows, then the one-launch tail */
@@ -256,8 +261,8 @@ int64_t tdp_launch_count(void);
                                    average solve them one CTA per system */
 #define TDP_TUNE_PER_SYSTEM_S 13 /* 1: tdp_solve_batched with s = 0 gives every system its own s (device model) */
 #define TDP_TUNE_IFACE32 14     /* 1: TDP_F32 and TDP_F32_REFINE solve the first level of their interface
-                                   recursion (interface systems above 2^19 rows) in binary32 arithmetic:
-                                   their Stage 3 reads the interface values as binary32 anyway */
+                                   recursion (interface systems above 2^19 rows) in binary32 arithmetic
+                                   (default 0: every interface level in binary64) */
 #define TDP_TUNE_REFINE_KEPT 15 /* 1: the refinement's second pass keeps the correction's Stage-1 coefficients
                                    (binary32) so that its last pass is elementwise (104 instead of 120 B/row) */
 #define TDP_TUNE_COOP_REG 16    /* 1: the one-launch interface tail reads its 8-row blocks into registers */
@@ -267,6 +272,12 @@ int64_t tdp_launch_count(void);
                                    interleaved tile (a quarter less shared memory per row) */
 #define TDP_TUNE_VTILE_L 19     /* 1: binary32 storage runs Stage 1 and Stage 3 on padded block-major tiles
                                    (each block's rows contiguous in shared memory) */
+#define TDP_TUNE_WINDOW 20      /* 1: TDP_F32_REFINE single systems and batches solved as one system take the
+                                   windowed single pass (see tdp_solve) */
+#define TDP_TUNE_WINDOW_HALO 21 /* halo rows on each side of a tile of the windowed pass [16, 64], even */
+#define TDP_TUNE_WAIT_LOG2 22   /* every bounded device wait gives up after 2^value clock cycles [10, 40] */
+#define TDP_TUNE_WAIT_NEVER 23  /* 1 (testing only): grid barriers wait for one arrival more than the grid has,
+                                   so every such wait runs out and the call reports TDP_ETIMEOUT */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 
@@ -294,27 +305,30 @@ int tdp_stage1(const void* a, const void* b, const void* c, const void* d, int64
 
 /* Allocation-free solve of one system (the paper has no counterpart; this
  * is a service of the library).  For callers that cannot allocate device
- * memory when they solve: code running while a stream is captured into a
- * CUDA graph (cudaMalloc is not permitted there), latency-critical loops in
- * which an allocation would synchronise the device, and hosts whose memory
- * pool owns all device memory.
+ * memory at the moment they solve: latency-critical loops in which a
+ * cudaMalloc would synchronise the device, and hosts whose memory pool owns
+ * all device memory and forbids other allocations after start-up.
  *
  * Same arguments and results as tdp_solve, for TDP_F64 and TDP_F32 only (no
- * refinement).  Scratch comes from one statically sized 16 MiB __device__
- * array inside the library, present on every GPU that loads the library
- * until the process exits; the call makes no cudaMalloc, cudaFree or other
- * device allocation.  Binary64 solves re-solve the interiors in Stage 3
- * instead of keeping per-row coefficients, so only the interface systems use
- * scratch: about 4.3 bytes per unknown at s = 32, i.e. n up to about 3.9
- * million unknowns at s = 32 (more with larger s).  Larger sizes are
- * rejected with TDP_EINVAL and a message giving the bytes needed.
+ * refinement); the tuning keys (tdp_set_tuning) apply as they do to
+ * tdp_solve.  Scratch comes from one statically sized 16 MiB __device__ array
+ * inside the library, present on every GPU that loads the library until the
+ * process exits; the call makes no cudaMalloc, cudaFree or other device
+ * allocation.  Binary64 solves re-solve the interiors in Stage 3 instead of
+ * keeping per-row coefficients, so only the interface systems use scratch:
+ * about 4.3 bytes per unknown at s = 32, i.e. n up to about 3.9 million
+ * unknowns at s = 32 (more with larger s).  Larger sizes are rejected with
+ * TDP_EINVAL and a message giving the bytes needed.
  *
  * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one array, which keeps
- * the previous call's contents (the status word is cleared at the start of
- * each call): calls whose work overlaps on the GPU (different streams, or
- * different host threads) race on it and must be serialised by the caller. */
+ * (cudaGetSymbolAddress, with that device current), once per device.  Every
+ * call shares the one array, which keeps the previous call's contents (the
+ * status word is cleared at the start of each call): calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  In checked mode (tdp_set_checked)
+ * the call synchronises its stream and maps the device status word like
+ * tdp_status_code; otherwise read it with the array's own status, which the
+ * next call clears. */
 int tdp_solve_noalloc(const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int32_t s,
                       tdp_dtype dtype, void* stream);
 

@@ -9,7 +9,8 @@ the rule it implements.
 * ``knn_predict``: k-nearest-neighbour classification (Sec. II-E: the mode of
   the labels of the k closest training sizes; k = 1 was found best).  The
   feature is log2 N (plus log2 batch when the table has batch sizes); the
-  paper used the SLAE size itself (reading recorded in the design notes).
+  paper used the SLAE size itself, but sizes here span 2^10 .. 2^28, so
+  distances are taken between their logarithms (a reading of Sec. II-E).
   Ties in distance are broken towards the larger s, ties in the vote likewise.
 * ``correct_labels``: the label correction of Sec. II-E.  The paper replaces
   noisy per-size optima by near-optimal sizes that follow the trend; its

@@ -24,6 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 F64, F32, F32_REFINE = 0, 1, 2
 _ERRORS = {1: "EINVAL", 2: "ECUDA", 3: "ESINGULAR", 4: "ETIMEOUT", 5: "ENOMEM"}
+OK, EINVAL, ECUDA, ESINGULAR, ETIMEOUT, ENOMEM = range(6)
 
 
 class TdpError(RuntimeError):
@@ -72,6 +73,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_recursion_plan.restype = I32
     lib.tdp_solve_multi.argtypes = [P, P, P, P, P, I64, I32, I64, I64, I32, I32, P]
     lib.tdp_solve_host.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
+    lib.tdp_status_code.argtypes = [ctypes.c_uint32]
     return lib
 
 
@@ -82,11 +84,14 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_load_table", "tdp_reserve", "tdp_status", "tdp_set_checked", "tdp_last_error",
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
-           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi", "tdp_solve_host")
+           "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi", "tdp_solve_host",
+           "tdp_status_code")
 
-(TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP, TUNE_FUSED_REFINE, TUNE_TMA, TUNE_PIPELINE,
- TUNE_WTILE, TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S,
- TUNE_IFACE32, TUNE_REFINE_KEPT, TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B, TUNE_VTILE_L) = range(20)
+(TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP) = range(5)
+(TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S, TUNE_IFACE32, TUNE_REFINE_KEPT,
+ TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B, TUNE_VTILE_L, TUNE_WINDOW, TUNE_WINDOW_HALO, TUNE_WAIT_LOG2,
+ TUNE_WAIT_NEVER) = range(9, 24)
+RETIRED_TUNING_KEYS = (5, 6, 7, 8)
 
 
 def _check(rc: int):

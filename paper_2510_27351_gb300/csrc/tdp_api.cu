@@ -69,44 +69,64 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // come from the environment: TDP_SMEM_BUDGET (shared memory per CTA aimed
 // for by the register-staged tiles), TDP_S_REC (sub-system size inside the
 // interface recursion), TDP_S_TAIL (inside its one-launch tail), TDP_VTILE,
-// TDP_COOP, TDP_FUSED_REFINE, TDP_TMA, TDP_PIPELINE, TDP_WTILE, TDP_REFINE3
-// (0/1 switches of the interleaved tiles, the one-launch tail, the fused
-// refinement passes, the TMA-staged tiles, the element-copy warp-tile
-// pipeline, the warp-owned bulk-copy tiles and the three-pass refinement),
-// TDP_RECURSION (1: the paper's recursion schedule), TDP_R (its number of
-// recursive steps, -1 = predicted), TDP_SEGMENTED (1: one CTA per system
-// for the interface systems of batches), TDP_PER_SYSTEM_S (1: batched
-// solves with s = 0 choose s per system on the device), TDP_IFACE32 (1:
-// the first level of the interface recursion of binary32 solves in binary32
-// arithmetic), TDP_REFINE_KEPT (1: the last refinement pass elementwise
-// from kept binary32 coefficients), TDP_COOP_REG (1: the one-launch tail
-// reads its 8-row blocks into registers), TDP_BATCH_FLAT (1: batches of
-// systems of at least 4096 rows on average are solved as one block-diagonal
-// system), TDP_VTILE_B (1: binary64 Stage 1 at s = 8 or 16 keeps b in
-// registers and a, c, d in the tile) and TDP_VTILE_L (1: binary32 storage
-// runs Stage 1 and Stage 3 on padded block-major tiles).
+// TDP_COOP, TDP_REFINE3 (0/1 switches of the interleaved tiles, the one-launch
+// tail and the three-pass refinement), TDP_RECURSION (1: the paper's
+// recursion schedule), TDP_R (its number of recursive steps, -1 =
+// predicted), TDP_SEGMENTED (1: one CTA per system for the interface systems
+// of batches), TDP_PER_SYSTEM_S (1: batched solves with s = 0 choose s per
+// system on the device), TDP_IFACE32 (1: the first level of the interface
+// recursion of binary32 solves in binary32 arithmetic), TDP_REFINE_KEPT (1:
+// the last refinement pass elementwise from kept binary32 coefficients),
+// TDP_COOP_REG (1: the one-launch tail reads its 8-row blocks into
+// registers), TDP_BATCH_FLAT (1: batches of systems of at least 4096 rows on
+// average are solved as one block-diagonal system), TDP_VTILE_B (1: binary64
+// Stage 1 at s = 8 or 16 keeps b in registers and a, c, d in the tile),
+// TDP_VTILE_L (1: binary32 storage runs Stage 1 and Stage 3 on padded
+// block-major tiles), TDP_WINDOW (1: the windowed single pass for binary32
+// solves with binary64 refinement), TDP_WINDOW_HALO (its halo rows per side),
+// TDP_WAIT_LOG2 (log2 of the clock-cycle budget of every bounded device wait)
+// and TDP_WAIT_NEVER (1: the grid barriers wait for one arrival more than
+// the grid has, so that every such wait runs out; for testing the timeout
+// path).  Keys 5 to 8 belonged to variants that were measured slower and
+// removed; they are rejected.
 struct Knob {
   const char* env;
   int lo, hi;
   std::atomic<int> v;
+  bool retired;
 };
-Knob g_knobs[20] = {
-    {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}}, {"TDP_S_REC", 3, 1024, {16}},
-    {"TDP_S_TAIL", 3, 256, {8}},                           {"TDP_VTILE", 0, 1, {1}},
-    {"TDP_COOP", 0, 1, {1}},                               {"TDP_FUSED_REFINE", 0, 1, {0}},
-    {"TDP_TMA", 0, 1, {0}},                                {"TDP_PIPELINE", 0, 1, {0}},
-    {"TDP_WTILE", 0, 1, {0}},                              {"TDP_REFINE3", 0, 1, {1}},
-    {"TDP_RECURSION", 0, 1, {0}},                          {"TDP_R", -1, 12, {-1}},
-    {"TDP_SEGMENTED", 0, 1, {1}},                          {"TDP_PER_SYSTEM_S", 0, 1, {0}},
-    {"TDP_IFACE32", 0, 1, {1}},                            {"TDP_REFINE_KEPT", 0, 1, {1}},
-    {"TDP_COOP_REG", 0, 1, {1}},                           {"TDP_BATCH_FLAT", 0, 1, {1}},
-    {"TDP_VTILE_B", 0, 1, {1}},                            {"TDP_VTILE_L", 0, 1, {1}},
+Knob g_knobs[24] = {
+    {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}, false},
+    {"TDP_S_REC", 3, 1024, {16}, false},
+    {"TDP_S_TAIL", 3, 256, {8}, false},
+    {"TDP_VTILE", 0, 1, {1}, false},
+    {"TDP_COOP", 0, 1, {1}, false},
+    {"(retired key 5)", 0, 0, {0}, true},
+    {"(retired key 6)", 0, 0, {0}, true},
+    {"(retired key 7)", 0, 0, {0}, true},
+    {"(retired key 8)", 0, 0, {0}, true},
+    {"TDP_REFINE3", 0, 1, {1}, false},
+    {"TDP_RECURSION", 0, 1, {0}, false},
+    {"TDP_R", -1, 12, {-1}, false},
+    {"TDP_SEGMENTED", 0, 1, {1}, false},
+    {"TDP_PER_SYSTEM_S", 0, 1, {0}, false},
+    {"TDP_IFACE32", 0, 1, {0}, false},
+    {"TDP_REFINE_KEPT", 0, 1, {1}, false},
+    {"TDP_COOP_REG", 0, 1, {1}, false},
+    {"TDP_BATCH_FLAT", 0, 1, {1}, false},
+    {"TDP_VTILE_B", 0, 1, {1}, false},
+    {"TDP_VTILE_L", 0, 1, {1}, false},
+    {"TDP_WINDOW", 0, 1, {1}, false},
+    {"TDP_WINDOW_HALO", 16, 64, {48}, false},
+    {"TDP_WAIT_LOG2", 10, 40, {31}, false},
+    {"TDP_WAIT_NEVER", 0, 1, {0}, false},
 };
 std::once_flag g_knobs_once;
 
 void knobs_init() {
   std::call_once(g_knobs_once, [] {
     for (Knob& k : g_knobs) {
+      if (k.retired) continue;
       if (const char* v = std::getenv(k.env)) {
         const int r = std::atoi(v);
         if (r >= k.lo && r <= k.hi) k.v.store(r);
@@ -115,17 +135,13 @@ void knobs_init() {
   });
 }
 
-void tune_from_env(Ctx& ctx) {
+void load_knobs(Ctx& ctx) {
   knobs_init();
   ctx.smem_budget = g_knobs[TDP_TUNE_SMEM_BUDGET].v.load();
   ctx.s_rec = g_knobs[TDP_TUNE_S_REC].v.load();
   ctx.s_tail = g_knobs[TDP_TUNE_S_TAIL].v.load();
   ctx.vtile = g_knobs[TDP_TUNE_VTILE].v.load() != 0;
   ctx.coop = g_knobs[TDP_TUNE_COOP].v.load() != 0;
-  ctx.fused_refine = g_knobs[TDP_TUNE_FUSED_REFINE].v.load() != 0;
-  ctx.tma = g_knobs[TDP_TUNE_TMA].v.load() != 0;
-  ctx.pipeline = g_knobs[TDP_TUNE_PIPELINE].v.load() != 0;
-  ctx.wtile = g_knobs[TDP_TUNE_WTILE].v.load() != 0;
   ctx.refine3 = g_knobs[TDP_TUNE_REFINE3].v.load() != 0;
   ctx.rec_mode = g_knobs[TDP_TUNE_RECURSION].v.load();
   ctx.rec_force = g_knobs[TDP_TUNE_R].v.load();
@@ -137,6 +153,10 @@ void tune_from_env(Ctx& ctx) {
   ctx.batch_flat = g_knobs[TDP_TUNE_BATCH_FLAT].v.load() != 0;
   ctx.vtile_b = g_knobs[TDP_TUNE_VTILE_B].v.load() != 0;
   ctx.vtile_l = g_knobs[TDP_TUNE_VTILE_L].v.load() != 0;
+  ctx.window = g_knobs[TDP_TUNE_WINDOW].v.load() != 0;
+  ctx.window_halo = g_knobs[TDP_TUNE_WINDOW_HALO].v.load();
+  ctx.wait_log2 = g_knobs[TDP_TUNE_WAIT_LOG2].v.load();
+  ctx.wait_never = g_knobs[TDP_TUNE_WAIT_NEVER].v.load() != 0;
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.
@@ -147,7 +167,7 @@ int run(void* stream, const char* fn, F&& driver) {
   Workspace* ws = workspace_for(st, &dev);
   Arena sizing;
   Ctx dry;
-  tune_from_env(dry);
+  load_knobs(dry);
   dry.stream = st;
   dry.ar = &sizing;
   dry.dry = true;
@@ -185,7 +205,7 @@ int run(void* stream, const char* fn, F&& driver) {
   arena.base = ws->buf;
   arena.cap = ws->cap;
   Ctx ctx;
-  tune_from_env(ctx);
+  load_knobs(ctx);
   ctx.stream = st;
   ctx.status = ws->status;
   ctx.ar = &arena;
@@ -200,9 +220,7 @@ int run(void* stream, const char* fn, F&& driver) {
     e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));
-    if (h & ST_BADARG) return set_error(TDP_EINVAL, std::string(fn) + ": offsets rejected on the device");
-    if (h & ST_TIMEOUT) return set_error(TDP_ETIMEOUT, std::string(fn) + ": device wait timed out");
-    if (h & ST_SINGULAR) return set_error(TDP_ESINGULAR, std::string(fn) + ": zero or non-finite pivot");
+    if (h) return status_error(h, fn);
   }
   g_last_error.clear();
   return TDP_OK;
@@ -274,6 +292,26 @@ int interval_rule(double n) {
 }  // namespace
 
 int set_last_error(int code, const std::string& msg) { return set_error(code, msg); }
+
+void tune_from_env(Ctx& ctx) { load_knobs(ctx); }
+// Return code of a device status word; when several bits are set the
+// argument error wins over a timeout, and a timeout over a pivot failure.
+int status_code(unsigned h) {
+  if (h & ST_BADARG) return TDP_EINVAL;
+  if (h & ST_TIMEOUT) return TDP_ETIMEOUT;
+  if (h & ST_SINGULAR) return TDP_ESINGULAR;
+  return TDP_OK;
+}
+
+int status_error(unsigned h, const char* fn) {
+  const int code = status_code(h);
+  const char* what = code == TDP_EINVAL     ? ": offsets rejected on the device"
+                     : code == TDP_ETIMEOUT ? ": device wait timed out"
+                     : code == TDP_ESINGULAR ? ": zero or non-finite pivot"
+                                            : "";
+  return set_last_error(code, std::string(fn) + what);
+}
+
 bool checked_mode() { return g_checked.load() != 0; }
 
 // ---------------------------------------------------------------------------
@@ -650,10 +688,7 @@ int tdp_status(void* stream) {
   e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
   if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string("tdp_status: ") + cudaGetErrorString(e));
-  if (h & ST_BADARG) return set_error(TDP_EINVAL, "tdp_status: offsets rejected on the device");
-  if (h & ST_TIMEOUT) return set_error(TDP_ETIMEOUT, "tdp_status: device wait timed out");
-  if (h & ST_SINGULAR) return set_error(TDP_ESINGULAR, "tdp_status: zero or non-finite pivot");
-  return TDP_OK;
+  return h ? status_error(h, "tdp_status") : TDP_OK;
 }
 
 void tdp_set_checked(int on) { g_checked.store(on ? 1 : 0); }
@@ -663,6 +698,7 @@ int tdp_set_tuning(int key, int value) {
   if (key < 0 || key >= int(sizeof(g_knobs) / sizeof(g_knobs[0])))
     return set_error(TDP_EINVAL, "tdp_set_tuning: unknown key");
   Knob& k = g_knobs[key];
+  if (k.retired) return set_error(TDP_EINVAL, "tdp_set_tuning: key " + std::to_string(key) + " is retired");
   if (value < k.lo || value > k.hi)
     return set_error(TDP_EINVAL, std::string("tdp_set_tuning: ") + k.env + " must be in [" + std::to_string(k.lo) +
                                      ", " + std::to_string(k.hi) + "]");
@@ -672,13 +708,15 @@ int tdp_set_tuning(int key, int value) {
 
 int tdp_get_tuning(int key) {
   knobs_init();
-  if (key < 0 || key >= int(sizeof(g_knobs) / sizeof(g_knobs[0]))) return -1;
+  if (key < 0 || key >= int(sizeof(g_knobs) / sizeof(g_knobs[0])) || g_knobs[key].retired) return -1;
   return g_knobs[key].v.load();
 }
 
 const char* tdp_last_error(void) { return g_last_error.c_str(); }
 
 int64_t tdp_launch_count(void) { return g_launches.load(); }
+
+int tdp_status_code(uint32_t bits) { return status_code(bits); }
 
 void tdp_profile_enable(int on) {
   profile_clear();

@@ -35,24 +35,31 @@ struct CoopParams {
   int reg;               // 1: blocks of 8 rows through registers (coop_block_reduce_reg)
   double* base_scratch;  // Thomas scratch for the last system
   double* ybase;         // solution of the last system (2 * lv[L-1].m rows)
+  long long wait_cycles; // a barrier wait gives up after this many clock cycles
+  unsigned bar_extra;    // arrivals a barrier waits for beyond the grid (0; 1 only to test the timeout)
 };
 
-// Grid-wide barrier.  bar[0] counts arrivals, bar[1] is the generation.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned* status) {
+// Grid-wide barrier.  bar[0] counts arrivals, bar[1] is the generation.  The
+// wait is bounded: after wait_cycles clock cycles the CTA raises ST_TIMEOUT
+// and every thread of it gets false (the kernel then returns).  With extra =
+// 1 the barrier waits for one arrival more than the grid has, so that it can
+// never complete (used only to test the timeout path).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned* status, long long wait_cycles,
+                                             unsigned extra) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
     volatile unsigned* gen = bar + 1;
     const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
-        if (clock64() - t0 > (1ll << 31)) {
+        if (clock64() - t0 > wait_cycles) {
           flag(status, ST_TIMEOUT);
           ok = 0;
           break;
@@ -294,8 +301,9 @@ __device__ __forceinline__ void coop_block_reduce_reg(const CoopLevel& D, int64_
 
 __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-__global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ CoopParams P, unsigned* bar,
-                                                    unsigned* status) {
+// Every level of P (down, base, up) with grid barriers between them; all
+// threads of the grid must call it.  Returns false once a barrier wait ran out.
+__device__ __forceinline__ bool coop_levels(const CoopParams& P, unsigned* bar, unsigned* status) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nth = int64_t(gridDim.x) * blockDim.x;
   bool ok = true;
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
       else
         coop_block_reduce(D, k, status);
     }
-    ok = grid_barrier(bar, status);
+    ok = grid_barrier(bar, status, P.wait_cycles, P.bar_extra);
   }
   if (ok && blockIdx.x == 0 && threadIdx.x < 32 && 2 * P.lv[P.L - 1].m <= 64) {
     const CoopLevel& D = P.lv[P.L - 1];
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
       P.ybase[i] = xn;
     }
   }
-  if (ok) ok = grid_barrier(bar, status);
+  if (ok) ok = grid_barrier(bar, status, P.wait_cycles, P.bar_extra);
   for (int l = P.L - 1; l >= 0 && ok; --l) {
     const CoopLevel& D = P.lv[l];
     const double* yn = (l == P.L - 1) ? P.ybase : P.lv[l + 1].y;
@@ -344,8 +352,14 @@ __global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ Coop
       const double2 v = *reinterpret_cast<const double2*>(yn + 2 * k);
       D.y[i] = fma(-D.kg[i], v.y, fma(-D.ka[i], v.x, D.kd[i]));
     }
-    if (l > 0) ok = grid_barrier(bar, status);
+    if (l > 0) ok = grid_barrier(bar, status, P.wait_cycles, P.bar_extra);
   }
+  return ok;
+}
+
+__global__ void __launch_bounds__(128) k_iface_coop(const __grid_constant__ CoopParams P, unsigned* bar,
+                                                    unsigned* status) {
+  coop_levels(P, bar, status);
 }
 
 }  // namespace tdp

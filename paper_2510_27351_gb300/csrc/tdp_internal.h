@@ -45,8 +45,6 @@ struct Ctx {
   cudaError_t err = cudaSuccess;
   int smem_budget = 100 * 1024;  // shared memory per CTA the launcher aims for
   int s_rec = 16;              // sub-system size inside the interface-system recursion
-  bool pipeline = false;       // warp-tile cp.async pipeline with element copies (TDP_PIPELINE=1)
-  bool wtile = false;          // warp-owned bulk-copy tiles (TDP_WTILE=1)
   bool refine3 = true;         // three fused passes for a solve and its first correction (TDP_REFINE3=0 off)
   int rec_mode = 0;            // 1: the paper's recursion schedule for the interface system (TDP_RECURSION)
   int rec_force = -1;          // its number of recursive steps; -1: predicted (TDP_R)
@@ -55,7 +53,7 @@ struct Ctx {
   tdp_dtype rec_dt = TDP_F64;
   bool seg = true;                   // per-system interface solves for batches (TDP_SEGMENTED=0 off)
   bool per_system_s = false;         // batched s = 0: one s per system from the device model (TDP_PER_SYSTEM_S=1)
-  bool iface32 = true;               // binary32 arithmetic in the first interface level of binary32 solves
+  bool iface32 = false;              // binary32 arithmetic in the first interface level of binary32 solves
   bool iface32_on = false;           // set while such a solve runs
   bool refine_kept = true;           // refinement pass 3 from kept binary32 coefficients (TDP_REFINE_KEPT)
   bool coop_reg = true;              // one-launch tail: 8-row blocks through registers (TDP_COOP_REG)
@@ -67,13 +65,15 @@ struct Ctx {
   int64_t seg_per = 0;                 // before each system (device), or blocks per system
   int32_t seg_batch = 0;
   bool events_ok = true;       // the profiler may create CUDA events around launches
-  bool tma = false;            // TMA-staged tiles (TDP_TMA=1); slower on GB300 so far
   bool vtile = true;           // 16-byte cp.async interleaved tiles for one system (TDP_VTILE=0 off)
   bool vtile_b = true;         // binary64 Stage 1 at s = 8, 16 with b in registers (TDP_VTILE_B=0 off)
   bool vtile_l = true;         // binary32 storage: padded block-major tiles (TDP_VTILE_L=0 off)
+  bool window = true;          // windowed single pass for binary32 + binary64 refinement (TDP_WINDOW=0 off)
+  int window_halo = 48;        // its halo rows on each side of a tile (TDP_WINDOW_HALO)
+  int wait_log2 = 31;          // bounded device waits give up after 2^wait_log2 cycles (TDP_WAIT_LOG2)
+  bool wait_never = false;     // testing: grid barriers can never complete (TDP_WAIT_NEVER)
   bool coop = true;            // small interface levels in one cooperative launch (TDP_COOP=0 off)
   int s_tail = 8;              // sub-system size inside that launch (TDP_S_TAIL)
-  bool fused_refine = false;   // one fused pass per refinement correction (TDP_FUSED_REFINE=1)
   std::string msg;
   void fail(cudaError_t e, const char* where) {
     if (err == cudaSuccess && e != cudaSuccess) {
@@ -87,6 +87,9 @@ struct Ctx {
 // brackets it with CUDA events on the launch stream (tdp_profile_*).
 void launch_begin(cudaStream_t st, const char* name, bool events_ok = true);
 void launch_end(cudaStream_t st);
+
+// Tuning knobs (tdp_set_tuning and the TDP_* environment variables) into ctx.
+void tune_from_env(Ctx& ctx);
 
 // Drivers.  Every pointer is a device pointer; all work is queued on ctx.stream.
 void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
@@ -113,6 +116,10 @@ void stage1_only(Ctx& ctx, const void* a, const void* b, const void* c, const vo
 // Error message of the calling host thread (tdp_last_error) and checked mode.
 int set_last_error(int code, const std::string& msg);
 bool checked_mode();
+// Return code of a device status word (ST_* bits) and the same with the
+// message recorded for fn.
+int status_code(unsigned bits);
+int status_error(unsigned bits, const char* fn);
 
 // Predictor (host 1-NN over the loaded table; tdp_api.cu).
 int32_t predict_s(int64_t n, int32_t batch, tdp_dtype dt);

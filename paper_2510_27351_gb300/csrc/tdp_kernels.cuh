@@ -492,142 +492,3 @@ __global__ void __launch_bounds__(128) k_thomas(const S* __restrict__ a, const S
 }
 
 }  // namespace tdp
-
-namespace tdp {
-
-// ---------------------------------------------------------------------------
-// One pass of binary32 + binary64 iterative refinement on a CTA tile (T
-// blocks, register-staged loads).  Given the interface values yc of the
-// correction system solved last (first pass: of A x = d) and the current
-// iterate xin (absent in the first pass), per block:
-//   1. r = d - A xin (binary64; d itself in the first pass),
-//   2. the interior of the correction solved in binary32 with yc at the
-//      block ends, xout = xin + delta in binary64,
-//   3. when another correction follows: r' = d - A xout (binary64) and the
-//      binary32 Stage 1 elimination of it, whose interface right-hand side
-//      goes to rd_next (the interface matrix is unchanged: same binary32
-//      pivots, computed by the same block_reduce as the first Stage 1).
-// Planes: 0 a, 1 b, 2 c, 3 d, 4 x, 5 r (binary64).
-// ---------------------------------------------------------------------------
-template <bool MAPPED, bool HAS_X>
-__global__ void __launch_bounds__(256) k_refine_pass_cta(const double* __restrict__ a, const double* __restrict__ b,
-                                                         const double* __restrict__ c, const double* __restrict__ d,
-                                                         const double* __restrict__ xin, int64_t n, int s,
-                                                         unsigned magic, int64_t m, const int64_t* __restrict__ blk,
-                                                         const double* __restrict__ yc, double* __restrict__ xout,
-                                                         double* __restrict__ rd_next,
-                                                         unsigned* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int T = blockDim.x, ld = T + 1, t = threadIdx.x;
-  const int64_t k0 = int64_t(blockIdx.x) * T;
-  if (k0 >= m) return;
-  const int nb = int(min(int64_t(T), m - k0));
-  const size_t plane = size_t(s) * ld;
-  double* P = reinterpret_cast<double*>(smem);
-  uint32_t* own = reinterpret_cast<uint32_t*>(P + 6 * plane);
-  TileGeom g{block_start<MAPPED>(k0, n, s, blk), block_start<MAPPED>(k0 + nb, n, s, blk), s, magic, ld, own};
-  BlockInfo bi{0, 0, true, true};
-  if (t < nb) bi = block_info<MAPPED>(k0 + t, n, s, m, blk);
-  int len_prev = 0;
-  if (t > 0 && t - 1 < nb) len_prev = block_info<MAPPED>(k0 + t - 1, n, s, m, blk).len;
-  if constexpr (MAPPED) {
-    if (t < nb) fill_owner(own, t, int(bi.start - g.ts), bi.len);
-    __syncthreads();
-  }
-  if constexpr (HAS_X) {
-    const double* src[5] = {a, b, c, d, xin};
-    double* dst[5] = {P, P + plane, P + 2 * plane, P + 3 * plane, P + 4 * plane};
-    tile_load<double, double, MAPPED, 5>(g, src, dst, n);
-  } else {
-    const double* src[4] = {a, b, c, d};
-    double* dst[4] = {P, P + plane, P + 2 * plane, P + 3 * plane};
-    tile_load<double, double, MAPPED, 4>(g, src, dst, n);
-  }
-  __syncthreads();
-  double* A = P + t;
-  double* Bp = P + plane + t;
-  double* Cp = P + 2 * plane + t;
-  double* D = P + 3 * plane + t;
-  double* X = P + 4 * plane + t;
-  double* R = P + 5 * plane + t;
-  const int len = bi.len;
-  const int64_t k = k0 + t;
-  // ---- 1. right-hand side of the correction system ----
-  if (t < nb && len > 0) {
-    for (int j = 0; j < len; ++j) {
-      double r = D[j * ld];
-      if constexpr (HAS_X) {
-        r = fma(-Bp[j * ld], X[j * ld], r);
-        if (j > 0) r = fma(-A[j * ld], X[(j - 1) * ld], r);
-        else if (!bi.first) r = fma(-A[0], t > 0 ? P[4 * plane + (len_prev - 1) * ld + (t - 1)] : xin[g.ts - 1], r);
-        if (j < len - 1) r = fma(-Cp[j * ld], X[(j + 1) * ld], r);
-        else if (!bi.last) r = fma(-Cp[j * ld], t + 1 < nb ? P[4 * plane + (t + 1)] : xin[g.te], r);
-      }
-      R[j * ld] = r;
-    }
-  }
-  __syncthreads();
-  // ---- 2. binary32 interior solve of the correction, binary64 update ----
-  if (t < nb && len > 0) {
-    const double2 yv = *reinterpret_cast<const double2*>(yc + 2 * k);
-    const float yl = narrow(yv.x), yr = narrow(yv.y);
-    if (len >= 3) {
-      float gam = 0.f, del = 0.f;
-      for (int j = 1; j <= len - 2; ++j) {
-        const float aj = narrow(A[j * ld]), bj = narrow(Bp[j * ld]),
-                    cj = narrow(Cp[j * ld]);
-        float rj = narrow(R[j * ld]);
-        if (j == 1) rj = fmaf(-aj, yl, rj);
-        if (j == len - 2) rj = fmaf(-cj, yr, rj);
-        const float den = (j == 1) ? bj : fmaf(-aj, gam, bj);
-        const float rc = rcp(den, status);
-        del = (j == 1) ? rj * rc : fmaf(-aj * rc, del, rj * rc);
-        gam = (j == len - 2) ? 0.f : cj * rc;
-        R[j * ld] = __hiloint2double(__float_as_int(gam), __float_as_int(del));  // (gamma, delta) of row j
-      }
-      float xn = del;
-      X[(len - 2) * ld] = (HAS_X ? X[(len - 2) * ld] : 0.0) + widen(xn);
-      for (int j = len - 3; j >= 1; --j) {
-        const double pk = R[j * ld];
-        xn = fmaf(-__int_as_float(__double2hiint(pk)), xn, __int_as_float(__double2loint(pk)));
-        X[j * ld] = (HAS_X ? X[j * ld] : 0.0) + widen(xn);
-      }
-    }
-    X[0] = (HAS_X ? X[0] : 0.0) + yv.x;
-    if (len >= 2) X[(len - 1) * ld] = (HAS_X ? X[(len - 1) * ld] : 0.0) + yv.y;
-  }
-  __syncthreads();
-  // ---- 3. residual of the update and the next interface right-hand side ----
-  if (rd_next) {
-    if (t < nb && len > 0) {
-      for (int j = 0; j < len; ++j) {
-        double r = fma(-Bp[j * ld], X[j * ld], D[j * ld]);
-        if (j > 0) {
-          r = fma(-A[j * ld], X[(j - 1) * ld], r);
-        } else if (!bi.first) {
-          const double xl = t > 0 ? P[4 * plane + (len_prev - 1) * ld + (t - 1)]
-                                  : (HAS_X ? xin[g.ts - 1] : 0.0) + yc[2 * k0 - 1];
-          r = fma(-A[0], xl, r);
-        }
-        if (j < len - 1) {
-          r = fma(-Cp[j * ld], X[(j + 1) * ld], r);
-        } else if (!bi.last) {
-          const double xr = t + 1 < nb ? P[4 * plane + (t + 1)] : (HAS_X ? xin[g.te] : 0.0) + yc[2 * (k0 + nb)];
-          r = fma(-Cp[j * ld], xr, r);
-        }
-        R[j * ld] = r;
-      }
-    }
-    __syncthreads();
-    if (t < nb) {
-      const IfaceRows ir = block_reduce<double, float, false>(A, Bp, Cp, R, ld, bi, status);
-      *reinterpret_cast<double2*>(rd_next + 2 * k) = make_double2(ir.d0, ir.d1);
-    }
-  }
-  __syncthreads();
-  const double* from[1] = {P + 4 * plane};
-  double* to[1] = {xout};
-  tile_store<double, double, MAPPED, 1>(g, from, to);
-}
-
-}  // namespace tdp

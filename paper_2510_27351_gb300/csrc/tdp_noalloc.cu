@@ -1,10 +1,9 @@
 // Allocation-free single-system solve.
 //
-// Some callers cannot allocate device memory at the moment they solve: code
-// that runs while a stream is being captured into a CUDA graph (cudaMalloc is
-// not allowed inside a capture), latency-critical loops where an allocation
-// would synchronise the device, or hosts whose memory pool owns all device
-// memory and forbids other allocations after start-up.  tdp_solve_noalloc
+// Some callers cannot allocate device memory at the moment they solve:
+// latency-critical loops where a cudaMalloc would synchronise the device, or
+// hosts whose memory pool owns all device memory and forbids other
+// allocations after start-up.  tdp_solve_noalloc
 // serves them: its scratch (the interface systems of every recursion level
 // and the status word) lives in one statically sized __device__ array that
 // the library image carries, so the call makes no cudaMalloc, cudaFree or
@@ -53,6 +52,7 @@ extern "C" int tdp_solve_noalloc(const void* a, const void* b, const void* c, co
   // size the scratch with a dry run of the driver; reject what does not fit
   Arena sizing;
   Ctx dry;
+  tune_from_env(dry);
   dry.stream = st;
   dry.ar = &sizing;
   dry.dry = true;
@@ -89,18 +89,21 @@ extern "C" int tdp_solve_noalloc(const void* a, const void* b, const void* c, co
   arena.base = static_cast<char*>(base) + kStatusBytes;
   arena.cap = kNoAllocBytes - kStatusBytes;
   Ctx ctx;
+  tune_from_env(ctx);
   ctx.stream = st;
   ctx.status = status;
   ctx.ar = &arena;
+  arena.err = &ctx.err;  // a take beyond the dry run's measure fails the call instead of aliasing
   ctx.events_ok = false;  // the profiler would create CUDA events
   solve_single_lean(ctx, a, b, c, d, x, n, ss, dtype);
-  if (ctx.err != cudaSuccess) return fail(TDP_ECUDA, "tdp_solve_noalloc: " + ctx.msg);
+  if (ctx.err != cudaSuccess)
+    return fail(TDP_ECUDA, "tdp_solve_noalloc: " + (ctx.msg.empty() ? std::string("scratch overrun") : ctx.msg));
   if (checked_mode()) {
     e = cudaStreamSynchronize(st);
     unsigned h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(TDP_ECUDA, std::string("tdp_solve_noalloc: ") + cudaGetErrorString(e));
-    if (h & ST_SINGULAR) return fail(TDP_ESINGULAR, "tdp_solve_noalloc: zero or non-finite pivot");
+    if (h) return status_error(h, "tdp_solve_noalloc");
   }
   return set_last_error(TDP_OK, "");
 }

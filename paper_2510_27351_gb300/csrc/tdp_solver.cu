@@ -13,12 +13,10 @@
 #include <vector>
 
 #include "tdp_internal.h"
-#include "tdp_tma.cuh"
 #include "tdp_vtile.cuh"
 #include "tdp_vtile_b.cuh"
 #include "tdp_vtile_l.cuh"
 #include "tdp_coop.cuh"
-#include "tdp_wtile.cuh"
 #include "tdp_refine.cuh"
 #include "tdp_const.cuh"
 #include "tdp_multi.cuh"
@@ -75,9 +73,7 @@ const char* tname(const char* f64, const char* f32) {
   return sizeof(C) == 8 ? f64 : f32;
 }
 
-// ---------------------------------------------------------------------------
-// Warp-tile pipeline geometry
-// ---------------------------------------------------------------------------
+// Number of SMs of the current device.
 int sm_count() {
   static int count[64] = {0};
   int dev = 0;
@@ -85,189 +81,6 @@ int sm_count() {
   if (dev < 0 || dev >= 64) dev = 0;
   if (!count[dev]) cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev);
   return count[dev] > 0 ? count[dev] : 1;
-}
-
-// Leading dimension of a warp tile: the smallest ld >= 32 whose element-copy
-// pattern (lane l copies tile row base + l, row p -> lane p / s, slot p % s)
-// needs the fewest shared-memory wavefronts, simulated bank by bank.
-int pick_ld(int s, int el) {
-  static std::mutex mu;
-  static std::map<std::pair<int, int>, int> memo;
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = memo.find({s, el});
-  if (it != memo.end()) return it->second;
-  int best = 1 << 30, best_ld = 33;
-  for (int ld = 32; ld < 32 + 64; ++ld) {
-    int worst = 0;
-    for (int base = 0; base < 32 * s; base += 32) {
-      int cost = 0;
-      const int group = (el == 8) ? 16 : 32;  // lanes served per 128-byte wavefront
-      for (int g0 = 0; g0 < 32; g0 += group) {
-        int hits[32] = {0};
-        int mx = 0;
-        for (int l = g0; l < g0 + group; ++l) {
-          const int p = base + l;
-          if (p >= 32 * s) continue;
-          const int t = p / s, j = p % s;
-          const int word = (j * ld + t) % group;
-          mx = std::max(mx, ++hits[word]);
-        }
-        cost += mx;
-      }
-      worst = std::max(worst, cost);
-    }
-    if (worst < best) {
-      best = worst;
-      best_ld = ld;
-    }
-  }
-  memo[{s, el}] = best_ld;
-  return best_ld;
-}
-
-size_t warp_bytes(int s, int ld, int el, bool mapped, int arrays) {
-  size_t b = size_t(arrays) * s * ld * el;
-  b = (b + 15) & ~size_t(15);
-  const size_t o = mapped ? size_t(32) * s * 4 : 0;
-  return 2 * (b + o);
-}
-
-// Leading dimension of a CTA tile of T blocks for the transpose pass (thread
-// i moves rows i, i + T, ...): the smallest ld >= T with the fewest
-// shared-memory wavefronts per warp, simulated bank by bank.
-int pick_ld_cta(int s, int el, int T) {
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, int> memo;
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = memo.find({s, el, T});
-  if (it != memo.end()) return it->second;
-  int best = 1 << 30, best_ld = T + 1;
-  const int group = (el == 8) ? 16 : 32;
-  for (int ld = T; ld < T + 64; ++ld) {
-    int worst = 0;
-    for (int base = 0; base < std::min(T * s, 32 * 64); base += 32) {
-      int cost = 0;
-      for (int g0 = 0; g0 < 32; g0 += group) {
-        int hits[32] = {0};
-        int mx = 0;
-        for (int l = g0; l < g0 + group; ++l) {
-          const int p = base + l;
-          const int t = p / s, j = p % s;
-          mx = std::max(mx, ++hits[(j * ld + t) % group]);
-        }
-        cost += mx;
-      }
-      worst = std::max(worst, cost);
-    }
-    if (worst < best) {
-      best = worst;
-      best_ld = ld;
-    }
-  }
-  memo[{s, el, T}] = best_ld;
-  return best_ld;
-}
-
-struct TmaCfg {
-  bool ok = false;
-  int T = 0, ld = 0, grid = 1;
-  size_t smem = 0;
-};
-
-template <typename S, bool MAPPED, int NA, typename K>
-TmaCfg tma_cfg(K kern, int s, int64_t m) {
-  TmaCfg c;
-  for (int T = 256; T >= 32; T /= 2) {
-    const int ld = pick_ld_cta(s, sizeof(S), T);
-    const size_t bytes = TmaBufs<S, MAPPED, NA>::bytes(T, s, ld);
-    if (bytes <= size_t(kMaxSmem)) {
-      c.T = T;
-      c.ld = ld;
-      c.smem = bytes;
-      break;
-    }
-  }
-  if (!c.T) return c;
-  allow_smem(kern);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.T, c.smem) != cudaSuccess || per_sm < 1)
-    return c;
-  const int64_t tiles = (m + c.T - 1) / c.T;
-  c.grid = int(std::max<int64_t>(1, std::min<int64_t>(tiles, int64_t(per_sm) * sm_count())));
-  c.ok = true;
-  return c;
-}
-
-constexpr size_t kPipeWarpMax = 113 * 1024;  // at least two warps per SM
-
-// Warps per CTA of the pipelined kernels (each warp has its own buffers, so
-// this only changes how the resident warps are grouped into CTAs).
-int pipe_warps() {
-  static int w = [] {
-    const char* v = std::getenv("TDP_PIPE_WARPS");
-    const int r = v ? std::atoi(v) : 1;
-    return (r >= 1 && r <= 4) ? r : 1;
-  }();
-  return w;
-}
-
-struct PipeCfg {
-  bool ok = false;
-  int ld = 33, warps = 1, grid = 1;
-  size_t smem = 0;
-};
-
-template <typename K>
-PipeCfg pipe_cfg(K kern, int s, int el, bool mapped, int64_t m, int arrays = 4) {
-  PipeCfg c;
-  c.ld = pick_ld(s, el);
-  const size_t per = warp_bytes(s, c.ld, el, mapped, arrays);
-  if (per > kPipeWarpMax) return c;
-  c.warps = int(std::min<size_t>(size_t(pipe_warps()), size_t(kMaxSmem) / per));
-  c.smem = per * c.warps;
-  allow_smem(kern);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * c.warps, c.smem) != cudaSuccess ||
-      per_sm < 1)
-    return c;
-  const int64_t tiles = (m + 31) / 32;
-  const int64_t want = (tiles + c.warps - 1) / c.warps;
-  c.grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(per_sm) * sm_count())));
-  c.ok = true;
-  return c;
-}
-
-// Warp-owned double-buffered block tiles (tdp_wtile.cuh): warps per CTA and
-// grid.  ok = false when fewer than three warps fit on an SM or the blocks
-// are not 16-byte aligned.
-struct WCfg {
-  bool ok = false;
-  int warps = 1;
-  unsigned grid = 1;
-  size_t smem = 0;
-};
-
-template <typename S, typename K>
-WCfg wtile_cfg(K kern, int s, int64_t m) {
-  WCfg c;
-  constexpr int V = Vec<S>::W;
-  if (s % V != 0) return c;
-  const size_t per = wwarp_bytes<S>(s);
-  if (per * 3 > size_t(kMaxSmem)) return c;
-  c.warps = int(std::min<size_t>(4, size_t(kMaxSmem) / per));
-  c.smem = per * c.warps;
-  allow_smem(kern);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * c.warps, c.smem) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    return c;
-  }
-  const int64_t tiles = (m + 31) / 32;
-  const int64_t want = (tiles + c.warps - 1) / c.warps;
-  c.grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(per_sm) * sm_count())));
-  c.ok = true;
-  return c;
 }
 
 // Padded block-major binary32 tiles (tdp_vtile_l.cuh): threads per CTA (=
@@ -293,18 +106,6 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
             const char* name = nullptr) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
   const char* nm = name ? name : KEEP ? "stage1_keep_f64" : tname<C>("stage1_f64", "stage1_f32");
-  if constexpr (!MAPPED && !KEEP && std::is_same<C, float>::value) {
-    if (ctx.wtile) {
-      auto wk = k_stage1_w<S>;
-      const WCfg wc = wtile_cfg<S>(wk, s, m);
-      if (wc.ok) {
-        pre_launch(ctx, nm);
-        wk<<<wc.grid, 32 * wc.warps, wc.smem, ctx.stream>>>(a, b, c, d, n, s, m, ra, rb, rc, rd, ctx.status);
-        post_launch(ctx, "stage 1");
-        return;
-      }
-    }
-  }
   if constexpr (!MAPPED && !KEEP && std::is_same<S, float>::value && std::is_same<C, float>::value) {
     if (ctx.vtile && ctx.vtile_l && s % 4 == 0) {
       // padded block-major tiles (tdp_vtile_l.cuh)
@@ -351,28 +152,6 @@ void stage1(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n,
       return;
     }
   }
-  if (ctx.tma) {
-    auto tk = k_stage1_tma<S, C, MAPPED, KEEP>;
-    const TmaCfg tc = tma_cfg<S, MAPPED, 4>(tk, s, m);
-    if (tc.ok) {
-      pre_launch(ctx, nm);
-      tk<<<tc.grid, tc.T, tc.smem, ctx.stream>>>(a, b, c, d, n, s, tc.ld, magic_for(s), m, blk, ra, rb, rc, rd, ka,
-                                                  kg, kd, ctx.status);
-      post_launch(ctx, "stage 1");
-      return;
-    }
-  }
-  if (ctx.pipeline) {
-    auto pk = k_stage1_pipe<S, C, MAPPED, KEEP>;
-    const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
-    if (pc.ok) {
-      pre_launch(ctx, nm);
-      pk<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(a, b, c, d, n, s, pc.ld, magic_for(s), m, blk, ra, rb,
-                                                           rc, rd, ka, kg, kd, ctx.status);
-      post_launch(ctx, "stage 1");
-      return;
-    }
-  }
   size_t smem;
   const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
   auto kern = k_stage1<S, C, MAPPED, KEEP>;
@@ -404,18 +183,6 @@ template <typename S, typename C, bool MAPPED>
 void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, int64_t n, int s, int64_t m,
                     const int64_t* blk, const double* y, S* x) {
   if (ctx.dry || ctx.err != cudaSuccess || m <= 0) return;
-  if constexpr (!MAPPED && std::is_same<C, float>::value) {
-    if (ctx.wtile) {
-      auto wk = k_stage3_resolve_w<S>;
-      const WCfg wc = wtile_cfg<S>(wk, s, m);
-      if (wc.ok) {
-        pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
-        wk<<<wc.grid, 32 * wc.warps, wc.smem, ctx.stream>>>(a, b, c, d, n, s, m, y, x, ctx.status);
-        post_launch(ctx, "stage 3");
-        return;
-      }
-    }
-  }
   if constexpr (!MAPPED && std::is_same<S, float>::value && std::is_same<C, float>::value) {
     if (ctx.vtile && ctx.vtile_l && s % 4 == 0) {
       const int64_t kb = ctx.kb, ke = ctx.ke >= 0 ? ctx.ke : m;
@@ -440,27 +207,6 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
                                                                  ctx.flat_nsys, kb, ke, ctx.status);
     post_launch(ctx, "stage 3");
     return;
-  }
-  if (ctx.tma) {
-    auto tk = k_stage3_resolve_tma<S, C, MAPPED>;
-    const TmaCfg tc = tma_cfg<S, MAPPED, 4>(tk, s, m);
-    if (tc.ok) {
-      pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
-      tk<<<tc.grid, tc.T, tc.smem, ctx.stream>>>(a, b, c, d, n, s, tc.ld, magic_for(s), m, blk, y, x, ctx.status);
-      post_launch(ctx, "stage 3");
-      return;
-    }
-  }
-  if (ctx.pipeline) {
-    auto pk = k_stage3_resolve_pipe<S, C, MAPPED>;
-    const PipeCfg pc = pipe_cfg(pk, s, sizeof(S), MAPPED, m);
-    if (pc.ok) {
-      pre_launch(ctx, tname<C>("stage3_resolve_f64", "stage3_resolve_f32"));
-      pk<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(a, b, c, d, n, s, pc.ld, magic_for(s), m, blk, y, x,
-                                                           ctx.status);
-      post_launch(ctx, "stage 3");
-      return;
-    }
   }
   size_t smem;
   const int T = pick_threads(ctx, s, 4, sizeof(C), MAPPED, &smem);
@@ -509,6 +255,8 @@ void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const do
   }
   P.L = L;
   P.reg = ctx.coop_reg ? 1 : 0;
+  P.wait_cycles = 1ll << ctx.wait_log2;
+  P.bar_extra = ctx.wait_never ? 1u : 0u;
   P.base_scratch = ctx.ar->take<double>(Ml);
   P.ybase = (L > 0) ? ctx.ar->take<double>(Ml) : y;
   unsigned* bar = ctx.ar->take<unsigned>(2);
@@ -884,85 +632,6 @@ unsigned grid_for(int64_t n, int threads) {
 }
 
 // ---------------------------------------------------------------------------
-// Refinement with the fused CTA-tile pass (k_refine_pass_cta).  Same
-// schedule as refine_fused; HBM traffic 4 + 5 + 6q words per row for q
-// corrections.
-// ---------------------------------------------------------------------------
-template <bool MAPPED>
-bool refine_fused_cta(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
-                      int s, int64_t m, const int64_t* blk, double* ra, double* rb, double* rc, double* rd, double* y,
-                      int iters) {
-  auto bytes = [&](int T) { return size_t(6) * 8 * s * (T + 1) + (MAPPED ? size_t(4) * T * s : 0); };
-  int T = 256;
-  while (T > 32 && bytes(T) > size_t(ctx.smem_budget)) T /= 2;
-  while (T > 1 && bytes(T) > size_t(kMaxSmem)) --T;
-  if (bytes(T) > size_t(kMaxSmem)) return false;
-  const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
-  double* rd2 = ctx.ar->take<double>(iters > 0 ? 2 * m : 1);
-  double* xb[2] = {ctx.ar->take<double>(iters > 0 ? n : 1), ctx.ar->take<double>(iters > 1 ? n : 1)};
-  stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
-                                       (float*)nullptr, (float*)nullptr);
-  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
-  for (int it = 0; it <= iters; ++it) {
-    const double* xin = it == 0 ? nullptr : xb[(it - 1) & 1];
-    double* xo = it == iters ? (double*)x : xb[it & 1];
-    double* rdn = it < iters ? rd2 : nullptr;
-    if (!ctx.dry && ctx.err == cudaSuccess) {
-      auto kern = it == 0 ? k_refine_pass_cta<MAPPED, false> : k_refine_pass_cta<MAPPED, true>;
-      allow_smem(kern);
-      pre_launch(ctx, "refine_pass");
-      kern<<<unsigned((m + T - 1) / T), T, bytes(T), ctx.stream>>>(A, B, Cc, D, xin, n, s, magic_for(s), m, blk, y,
-                                                                   xo, rdn, ctx.status);
-      post_launch(ctx, "refine pass");
-    }
-    if (it < iters) solve_interface(ctx, ra, rb, rc, rd2, y, 2 * m);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// Refinement with the fused pass (k_refine_pass): Stage 1 in binary32, then
-// per correction one pass that finishes the previous correction, updates x
-// in binary64 and prepares the next interface right-hand side.  HBM traffic
-// for q corrections: 4 + 5 + 6q words per row.  Returns false (and queues
-// nothing) when the warp tile does not fit in shared memory.
-// ---------------------------------------------------------------------------
-template <bool MAPPED>
-bool refine_fused(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
-                  int64_t m, const int64_t* blk, double* ra, double* rb, double* rc, double* rd, double* y,
-                  int iters) {
-  if (!ctx.fused_refine) return false;
-  if (!ctx.pipeline) return refine_fused_cta<MAPPED>(ctx, a, b, c, d, x, n, s, m, blk, ra, rb, rc, rd, y, iters);
-  const size_t per = warp_bytes(s, pick_ld(s, 8), 8, MAPPED, 6);
-  if (per > kPipeWarpMax) return false;
-  const double *A = (const double*)a, *B = (const double*)b, *Cc = (const double*)c, *D = (const double*)d;
-  double* rd2 = ctx.ar->take<double>(iters > 0 ? 2 * m : 1);
-  double* xb[2] = {ctx.ar->take<double>(iters > 0 ? n : 1), ctx.ar->take<double>(iters > 1 ? n : 1)};
-  stage1<double, float, MAPPED, false>(ctx, A, B, Cc, D, n, s, m, blk, ra, rb, rc, rd, (float*)nullptr,
-                                       (float*)nullptr, (float*)nullptr);
-  solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
-  for (int it = 0; it <= iters; ++it) {
-    const double* xin = it == 0 ? nullptr : xb[(it - 1) & 1];
-    double* xo = it == iters ? (double*)x : xb[it & 1];
-    double* rdn = it < iters ? rd2 : nullptr;
-    if (!ctx.dry && ctx.err == cudaSuccess) {
-      auto kern = it == 0 ? k_refine_pass<MAPPED, false> : k_refine_pass<MAPPED, true>;
-      const PipeCfg pc = pipe_cfg(kern, s, 8, MAPPED, m, 6);
-      if (!pc.ok) {
-        ctx.fail(cudaErrorInvalidConfiguration, "refine pass configuration");
-        return true;
-      }
-      pre_launch(ctx, "refine_pass");
-      kern<<<pc.grid, 32 * pc.warps, pc.smem, ctx.stream>>>(A, B, Cc, D, xin, n, s, pc.ld, magic_for(s), m, blk, y,
-                                                             xo, rdn, ctx.status);
-      post_launch(ctx, "refine pass");
-    }
-    if (it < iters) solve_interface(ctx, ra, rb, rc, rd2, y, 2 * m);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
 // One solve over blocks given either arithmetically (one system) or by blk.
 // ---------------------------------------------------------------------------
 template <bool MAPPED>
@@ -990,8 +659,6 @@ void solve_blocks(Ctx& ctx, const void* a, const void* b, const void* c, const v
                                 (T*)nullptr);
     solve_interface(ctx, ra, rb, rc, rd, y, 2 * m);
     stage3_resolve<T, T, MAPPED>(ctx, A, B, Cc, D, n, s, m, blk, y, (T*)x);
-  } else if (refine_fused<MAPPED>(ctx, a, b, c, d, x, n, s, m, blk, ra, rb, rc, rd, y, refine_iters)) {
-    // binary32 eliminations, binary64 residual and correction, one fused pass per correction
   } else if (ctx.refine3 && refine_iters >= 1) {
     // three passes for the solve and its first correction (tdp_refine.cuh), then
     // separate kernels for any further correction
@@ -1407,7 +1074,7 @@ bool flat_batch(const Ctx& ctx, int32_t batch, int64_t total_n, tdp_dtype dt, in
   if (!ctx.batch_flat || batch < 2 || total_n < int64_t(batch) * 4096) return false;
   if (dt == TDP_F32_REFINE) return true;
   const int V = dt == TDP_F64 ? 2 : 4;
-  return ctx.vtile && !ctx.wtile && s % V == 0;
+  return ctx.vtile && s % V == 0;
 }
 
 void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
@@ -1415,8 +1082,7 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
   if (s > total_n) s = int(std::max<int64_t>(2, total_n));
   const int64_t m = (total_n + s - 1) / s;
   const bool cut_in_tiles = dt != TDP_F32_REFINE ||
-                            (refine_iters == 1 && ctx.refine3 && ctx.refine_kept && !ctx.fused_refine &&
-                             !ctx.wtile && !ctx.tma && !ctx.pipeline);
+                            (refine_iters == 1 && ctx.refine3 && ctx.refine_kept);
   if (cut_in_tiles) {
     FlatScope fs(ctx, offsets, batch);
     solve_blocks<false>(ctx, a, b, c, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);
@@ -1458,8 +1124,7 @@ void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const voi
   char* xd = ctx.ar->take<char>(size_t(n) * el);
   const char* hsrc[4] = {(const char*)a, (const char*)b, (const char*)c, (const char*)d};
   char* dsrc[4] = {ad, bd, cd, dd};
-  const bool chunked = ctx.vtile && !ctx.tma && !ctx.pipeline &&
-                       (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0 && !ctx.wtile));
+  const bool chunked = ctx.vtile && (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0));
   if (!chunked) {
     if (!ctx.dry && ctx.err == cudaSuccess)
       for (int i = 0; i < 4; ++i)

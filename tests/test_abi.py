@@ -126,12 +126,25 @@ def test_tuning_knobs_validate_and_round_trip():
         assert tdp.tdp_get_tuning(99) == -1
         assert tdp.tdp_get_tuning(tdp.TUNE_S_REC) == 16
         # every key the header declares answers with its default range
-        defaults = {tdp.TUNE_IFACE32: 1, tdp.TUNE_REFINE_KEPT: 1, tdp.TUNE_SEGMENTED: 1, tdp.TUNE_REFINE3: 1,
+        defaults = {tdp.TUNE_IFACE32: 0, tdp.TUNE_REFINE_KEPT: 1, tdp.TUNE_SEGMENTED: 1, tdp.TUNE_REFINE3: 1,
                     tdp.TUNE_PER_SYSTEM_S: 0, tdp.TUNE_VTILE: 1, tdp.TUNE_COOP: 1, tdp.TUNE_COOP_REG: 1,
-                    tdp.TUNE_BATCH_FLAT: 1, tdp.TUNE_VTILE_B: 1, tdp.TUNE_VTILE_L: 1, tdp.TUNE_TMA: 0,
-                    tdp.TUNE_PIPELINE: 0, tdp.TUNE_WTILE: 0, tdp.TUNE_FUSED_REFINE: 0}
+                    tdp.TUNE_BATCH_FLAT: 1, tdp.TUNE_VTILE_B: 1, tdp.TUNE_VTILE_L: 1, tdp.TUNE_WINDOW: 1,
+                    tdp.TUNE_WAIT_NEVER: 0}
         for key, v in defaults.items():
             assert tdp.tdp_get_tuning(key) in (0, 1) and tdp.tdp_get_tuning(key) == v, key
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO) == 48
+        assert tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2) == 31
+        # the binary32 interface level is off by default: every interface
+        # level of every precision runs in binary64 (the reduced system's
+        # stability is what binary64 is kept for)
+        for key in tdp.RETIRED_TUNING_KEYS:
+            assert tdp.tdp_get_tuning(key) == -1
+            with pytest.raises(tdp.TdpError, match="retired"):
+                tdp.tdp_set_tuning(key, 0)
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, 8)
+        with pytest.raises(tdp.TdpError):
+            tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 41)
         with pytest.raises(tdp.TdpError):
             tdp.tdp_set_tuning(tdp.TUNE_IFACE32, 2)
         with pytest.raises(tdp.TdpError):
@@ -139,7 +152,7 @@ def test_tuning_knobs_validate_and_round_trip():
         tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, 0)
         assert tdp.tdp_get_tuning(tdp.TUNE_VTILE_L) == 0
         tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, 1)
-        assert tdp.tdp_get_tuning(tdp.TUNE_VTILE_L + 1) == -1
+        assert tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER + 1) == -1
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_S_REC, old)
 
@@ -221,3 +234,19 @@ def test_builtin_recursion_depth_model_matches_the_oracle_knn():
             want = P.knn_predict([r[0] for r in mine], [r[2] for r in mine], n, k=1,
                                  train_batches=[r[1] for r in mine], query_batch=1)
             assert tdp.tdp_predict_r(n, 1, dt) == want, (dt, n)
+
+
+def test_status_word_maps_to_return_codes():
+    """Host-only: every bit of the device status word maps to its return
+    code, with the precedence argument error > timeout > pivot failure that
+    tdp_status, checked-mode solves and tdp_solve_noalloc share."""
+    import paper_2510_27351_gb300 as tdp
+
+    SING, TIME, BAD = 1, 2, 4
+    assert tdp.LIB.tdp_status_code(0) == tdp.OK
+    assert tdp.LIB.tdp_status_code(SING) == tdp.ESINGULAR
+    assert tdp.LIB.tdp_status_code(TIME) == tdp.ETIMEOUT
+    assert tdp.LIB.tdp_status_code(BAD) == tdp.EINVAL
+    assert tdp.LIB.tdp_status_code(SING | TIME) == tdp.ETIMEOUT
+    assert tdp.LIB.tdp_status_code(SING | BAD) == tdp.EINVAL
+    assert tdp.LIB.tdp_status_code(SING | TIME | BAD) == tdp.EINVAL

@@ -41,6 +41,17 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
+def per_system_err(x, ref, offsets):
+    """Largest relative infinity-norm error over the systems of a batch (so
+    that a short system's error is not hidden behind a long one's norm)."""
+    worst = 0.0
+    for j in range(len(offsets) - 1):
+        lo, hi = int(offsets[j]), int(offsets[j + 1])
+        if hi > lo:
+            worst = max(worst, oracle.rel_err(x[lo:hi], ref[lo:hi]))
+    return worst
+
+
 def _solve(tdp, S, s, code, iters=1):
     import torch
 
@@ -131,7 +142,7 @@ def test_batched_uneven(tdp, code):
         x = torch.empty_like(d)
         tdp.tdp_solve_batched(off, len(sizes), Sb.n, a, b, c, d, x, s, code, 1 if code == 2 else 0)
         torch.cuda.synchronize()
-        e = oracle.rel_err(host(x), ref)
+        e = per_system_err(host(x), ref, Sb.offsets)
         assert e <= TOL[code], (s, e)
 
 
@@ -146,7 +157,7 @@ def test_batched_log_uniform_small(tdp):
         x = torch.empty_like(d)
         tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, 0, code, 1 if code == 2 else 0)
         torch.cuda.synchronize()
-        assert oracle.rel_err(host(x), ref) <= 1e-12
+        assert per_system_err(host(x), ref, Sb.offsets) <= 1e-12
 
 
 def test_bad_offsets_reported(tdp):
@@ -284,7 +295,7 @@ def test_batched_per_system_sizes(tdp, tmp_path):
             x = torch.empty_like(d)
             tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, 0, code, 1 if code == 2 else 0)
             torch.cuda.synchronize()
-            assert oracle.rel_err(host(x), ref) <= 1e-12, code
+            assert per_system_err(host(x), ref, Sb.offsets) <= 1e-12, code
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_PER_SYSTEM_S, old)
         tdp.tdp_load_table("")
@@ -315,63 +326,6 @@ def test_cuda_graph_capture_and_autotune(tdp):
         tdp.tdp_status()
     finally:
         tdp.tdp_set_checked(True)
-
-
-@pytest.mark.parametrize("code", [1, 2])
-def test_warp_bulk_tiles(tdp, code):
-    """The opt-in warp-owned bulk-copy tiles (TDP_TUNE_WTILE) against the oracle:
-    sizes with a ragged last block, an array end inside a 16-byte chunk, and
-    several tiles per warp."""
-    old = tdp.tdp_get_tuning(tdp.TUNE_WTILE)
-    tdp.tdp_set_tuning(tdp.TUNE_WTILE, 1)
-    try:
-        for n in (2, 3, 5, 63, 64, 65, 1000, 4097, 100_003, 1 << 20):
-            S = W.single(n, seed=n + 7)
-            ref = oracle.thomas(S.a, S.b, S.c, S.d)
-            for s in (2, 4, 8, 12, 24, 32, 64, 100, 128):
-                e = oracle.rel_err(_solve(tdp, S, s, code), ref)
-                assert e <= TOL[code], (n, s, e)
-    finally:
-        tdp.tdp_set_tuning(tdp.TUNE_WTILE, old)
-
-
-@pytest.mark.parametrize("knobs", [("TUNE_TMA",), ("TUNE_PIPELINE",), ("TUNE_FUSED_REFINE",),
-                                   ("TUNE_FUSED_REFINE", "TUNE_PIPELINE")])
-def test_opt_in_tile_variants(tdp, knobs):
-    """The opt-in tile variants kept for measurement (CTA-wide bulk copies
-    with a transpose pass, per-warp element-copy pipelines, the fused
-    refinement passes) against the oracle, with the interleaved tiles off so
-    that every tile kernel takes them: ragged last blocks, an array end inside
-    a 16-byte chunk, several tiles per CTA, and a batch with the block map."""
-    keys = [getattr(tdp, k) for k in knobs] + [tdp.TUNE_VTILE]
-    old = [tdp.tdp_get_tuning(k) for k in keys]
-    for k in keys[:-1]:
-        tdp.tdp_set_tuning(k, 1)
-    tdp.tdp_set_tuning(tdp.TUNE_VTILE, 0)
-    codes = (2,) if "TUNE_FUSED_REFINE" in knobs else (0, 1, 2)
-    try:
-        for n in (5, 63, 1000, 4097, 100_003, 1 << 20):
-            S = W.single(n, seed=n + 3)
-            ref = oracle.thomas(S.a, S.b, S.c, S.d)
-            for code in codes:
-                for s in (3, 8, 24, 64):
-                    e = oracle.rel_err(_solve(tdp, S, s, code), ref)
-                    assert e <= TOL[code], (knobs, n, code, s, e)
-        import torch
-
-        Sb = W.batched(64, 2, 3000, seed=5)
-        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
-        off = dev(Sb.offsets)
-        for code in codes:
-            dt = torch.float32 if code == 1 else torch.float64
-            a, b, c, d = (dev(v, dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
-            x = torch.empty_like(d)
-            tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, 8, code, 1 if code == 2 else 0)
-            torch.cuda.synchronize()
-            assert oracle.rel_err(host(x), ref) <= TOL[code], (knobs, code)
-    finally:
-        for k, v in zip(keys, old):
-            tdp.tdp_set_tuning(k, v)
 
 
 @pytest.mark.parametrize("code", [0, 1, 2])
@@ -519,12 +473,13 @@ def test_refinement_last_pass_variants(tdp, kept):
         tdp.tdp_set_tuning(tdp.TUNE_REFINE_KEPT, old)
 
 
-@pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 0),
+@pytest.mark.parametrize("key,value", [("TUNE_VTILE", 0), ("TUNE_COOP_REG", 0), ("TUNE_IFACE32", 1),
                                        ("TUNE_VTILE_B", 0), ("TUNE_VTILE_L", 0)])
 def test_tuning_variants(tdp, key, value):
     """Non-default kernel choices give the same answers: register-staged
     tiles instead of the interleaved cp.async tiles, the one-launch tail
-    without register-resident blocks, every interface level in binary64,
+    without register-resident blocks, the first interface level of the
+    binary32 solves in binary32 arithmetic,
     binary32 full blocks on the interleaved tiles.  Sizes reach the
     interface levels above 2^19 rows."""
     k = getattr(tdp, key)
@@ -736,3 +691,128 @@ def test_solve_host_arrays(tdp, code):
             tdp.tdp_solve(*[h.cuda() for h in hs], dev_x, n, s, code, it)
             torch.cuda.synchronize()
             assert np.array_equal(host(dev_x), got), (n, s, code, pinned)
+
+
+def test_device_wait_timeout_reported(tdp):
+    """Failure detection without a GPU fault: with the testing key
+    TDP_TUNE_WAIT_NEVER the grid barrier of the one-launch interface solve
+    waits for an arrival that never comes; every wait gives up after
+    2^14 cycles, the kernel returns, and the call reports TDP_ETIMEOUT.  The
+    context stays usable: the same solve then matches the oracle."""
+    import torch
+
+    n, s = 1 << 20, 16  # interface system of 131,072 rows: one cooperative launch
+    S = W.single(n, seed=31)
+    ref = oracle.thomas(S.a, S.b, S.c, S.d)
+    old = (tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER), tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2))
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 14)
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, 1)
+    try:
+        for code in (0, 1, 2):
+            with pytest.raises(tdp.TdpError) as ei:
+                _solve(tdp, S, s, code)
+            assert ei.value.code == tdp.ETIMEOUT, code
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
+    for code in (0, 2):
+        assert oracle.rel_err(_solve(tdp, S, s, code), ref) <= TOL[code]
+    # unchecked mode: the call returns at once and tdp_status reports the timeout later
+    tdp.tdp_set_checked(False)
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 14)
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, 1)
+    try:
+        _solve(tdp, S, s, 0)
+        with pytest.raises(tdp.TdpError) as ei:
+            tdp.tdp_status()
+        assert ei.value.code == tdp.ETIMEOUT
+        tdp.tdp_status()  # cleared by the read
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
+        tdp.tdp_set_checked(True)
+
+
+def test_device_size_model_matches_the_oracle_knn(tdp):
+    """The size model's inference kernel (tdp_predict_s_batched, one system
+    per thread) against the oracle's 1-NN over the built-in table (Sec. II-E:
+    log2 N and log2 batch features, ties to the larger s): every table size,
+    sizes between and around them, for several batch sizes."""
+    import os
+
+    import torch
+
+    from oracle import predictor as P
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rows = P.load_table(os.path.join(root, "paper_2510_27351_gb300", "data", "table_gb300.txt"))
+    for dt in (0, 1, 2):
+        mine = [(int(r[1]), int(r[2]), int(r[3])) for r in rows if int(r[0]) == dt]
+        ns = sorted({n for n, _, _ in mine})
+        queries = set(ns) | {1, 2, 100, 1 << 29}
+        queries |= {int((x * y) ** 0.5) for x, y in zip(ns, ns[1:])}
+        queries |= {n + 1 for n in ns} | {n - 1 for n in ns}
+        queries = sorted(q for q in queries if q >= 1)
+        for batch in (1, 2, 64, 1024, 4096):
+            groups = [[q] for q in queries] if batch == 1 else [[queries[i % len(queries)] for i in range(batch)]]
+            for sizes in groups:
+                off = np.zeros(len(sizes) + 1, dtype=np.int64)
+                np.cumsum(np.asarray(sizes, dtype=np.int64), out=off[1:])
+                out = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+                tdp.tdp_predict_s_batched(dev(off), len(sizes), dt, out)
+                torch.cuda.synchronize()
+                got = out.cpu().numpy()
+                for q, g in zip(sizes, got):
+                    want = P.knn_predict([r[0] for r in mine], [r[2] for r in mine], q, k=1,
+                                         train_batches=[r[1] for r in mine], query_batch=len(sizes))
+                    assert int(g) == want, (dt, q, len(sizes), int(g), want)
+
+
+def test_adjoint_central_differences(tdp):
+    """The adjoint through the autograd Function against central differences
+    on the device (h = 1e-6, every entry of a, b, c and d): systems of N = 64
+    drawn like the 1024 x 8192 differentiation workload, loss L = sum(w x),
+    w ~ N(0, 1).  All 2 x 4 x 64 perturbed systems of one base system are
+    solved as one batch.  Agreement to 1e-6 relative (truncation O(h^2) and
+    rounding O(eps / h) are both far below)."""
+    import torch
+
+    n, h = 64, 1e-6
+    Sb = W.uniform_batch(4, n, seed=41)
+    wts = W.loss_weights(Sb.n, seed=41)
+    for j in range(4):
+        lo, hi = j * n, (j + 1) * n
+        base = [v[lo:hi].copy() for v in (Sb.a, Sb.b, Sb.c, Sb.d)]
+        w = wts[lo:hi]
+        ts = [dev(v).requires_grad_(True) for v in base]
+        x = tdp.tridiagonal_solve(*ts, s=8)
+        (dev(w) * x).sum().backward()
+        grads = [host(t.grad) for t in ts]
+        # batch of perturbed copies: for each array k and entry i, +h then -h
+        P = 2 * 4 * n
+        A = np.tile(base[0], P); B = np.tile(base[1], P); C = np.tile(base[2], P); D = np.tile(base[3], P)
+        arrs = (A, B, C, D)
+        q = 0
+        for k in range(4):
+            for i in range(n):
+                for sign in (1.0, -1.0):
+                    arrs[k][q * n + i] += sign * h
+                    q += 1
+        off = np.arange(P + 1, dtype=np.int64) * n
+        X = torch.empty(P * n, dtype=torch.float64, device="cuda")
+        tdp.tdp_solve_batched(dev(off), P, P * n, dev(A), dev(B), dev(C), dev(D), X, 8, tdp.F64, 0)
+        torch.cuda.synchronize()
+        L = (host(X).reshape(P, n) * w[None, :]).sum(axis=1)
+        fd = ((L[0::2] - L[1::2]) / (2 * h)).reshape(4, n)
+        for k in range(4):
+            g = grads[k].copy()
+            if k == 0:
+                g[0] = fd[k][0]  # a[0] is ignored by the solver: no dependence, zero gradient both ways
+            if k == 2:
+                g[-1] = fd[k][-1]
+            scale = np.max(np.abs(grads[k]))
+            assert np.max(np.abs(fd[k] - g)) <= 1e-6 * scale, ("abcd"[k], j, np.max(np.abs(fd[k] - g)) / scale)
+            if k == 0:
+                assert grads[0][0] == 0.0 and abs(fd[0][0]) <= 1e-6 * scale
+            if k == 2:
+                assert grads[2][-1] == 0.0 and abs(fd[2][-1]) <= 1e-6 * scale

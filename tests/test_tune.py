@@ -154,9 +154,9 @@ def test_committed_tables_are_derived_from_the_committed_sweeps(tmp_path):
 
 
 def test_committed_evaluations_are_reproduced_from_the_committed_sweeps():
-    """The evaluation reports quoted in the design notes (size model, recursion
-    depth model, transfer between precisions) are what tune.py computes from
-    the committed sweeps (fixed split seed)."""
+    """The committed evaluation reports (size model, recursion depth model,
+    transfer between precisions) are what tune.py computes from the committed
+    sweeps (fixed split seed)."""
     import json
 
     from paper_2510_27351_gb300 import tune

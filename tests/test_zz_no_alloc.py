@@ -1,17 +1,19 @@
 """The allocation-free entry point, tdp_solve_noalloc.
 
 It exists for callers that cannot allocate device memory when they solve
-(inside CUDA graph capture, in latency-critical loops, or under a host
-memory pool that owns all device memory): its scratch is a static 16 MiB
-device array inside the library.  These tests call it through the C ABI
-and compare it with tdp_solve, within the tolerances the other GPU tests use
-(binary64 1e-12, binary32 1e-5, relative infinity norm), on two calls in a
-row, so that state the shared array keeps from one call cannot leak into the
-next.  The file is collected last on purpose.
+(latency-critical loops where a cudaMalloc would synchronise the device, or
+a host memory pool that owns all device memory): its scratch is a static
+16 MiB device array inside the library.  These tests call it through the C
+ABI and compare it with tdp_solve and with the oracle's binary64 Thomas
+solve, within the tolerances the other GPU tests use (binary64 1e-12,
+binary32 1e-5, relative infinity norm), on two calls in a row, so that state
+the shared array keeps from one call cannot leak into the next.  The file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +54,7 @@ def test_noalloc_matches_tdp_solve_twice(tdp, code, tol):
         got = x.double().cpu().numpy()
         assert np.all(np.isfinite(got))
         assert _rel(got, ref) <= tol, (n, s, _rel(got, ref))
+        assert _rel(got, oracle.thomas(S.a, S.b, S.c, S.d)) <= tol, (n, s)
         assert _rel(got, S.xstar) <= (1e-12 if code == 0 else 1e-5)
 
 
@@ -68,3 +71,30 @@ def test_noalloc_rejects_oversized_systems(tdp):
     rc = tdp.LIB.tdp_solve_noalloc(a.data_ptr(), a.data_ptr(), a.data_ptr(), a.data_ptr(), a.data_ptr(), 1000, 32, 2,
                                    torch.cuda.current_stream().cuda_stream)
     assert rc == 1
+
+
+def test_noalloc_reports_a_device_timeout(tdp):
+    """A bounded device wait that runs out inside the allocation-free call
+    (the grid barrier of the one-launch interface solve, made unreachable by
+    the testing key TDP_TUNE_WAIT_NEVER) comes back as TDP_ETIMEOUT in
+    checked mode, like tdp_solve; afterwards the same call succeeds again."""
+    import torch
+
+    n, s = 1 << 20, 16  # interface system of 131,072 rows: solved in one cooperative launch
+    S = W.single(n, seed=21)
+    a, b, c, d = (torch.from_numpy(v).cuda() for v in (S.a, S.b, S.c, S.d))
+    x = torch.empty_like(d)
+    st = torch.cuda.current_stream().cuda_stream
+    args = (a.data_ptr(), b.data_ptr(), c.data_ptr(), d.data_ptr(), x.data_ptr(), n, s, 0, st)
+    old = (tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER), tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2))
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 14)
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, 1)
+    try:
+        assert tdp.LIB.tdp_solve_noalloc(*args) == tdp.ETIMEOUT
+        assert "timed out" in tdp.tdp_last_error()
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
+    assert tdp.LIB.tdp_solve_noalloc(*args) == tdp.OK, tdp.tdp_last_error()
+    torch.cuda.synchronize()
+    assert _rel(x.cpu().numpy(), oracle.thomas(S.a, S.b, S.c, S.d)) <= 1e-12

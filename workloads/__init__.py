@@ -28,6 +28,10 @@ Workloads (value distributions of the benchmark configurations)
   Dirichlet zeros outside the grid (the solver ignores a at a line's first
   row and c at its last, so one materialised diagonal serves the row and the
   column sweep), field u ~ U[0, 1].
+* ``weak``: near-weakly-dominant systems: a, c ~ U[-1, 1] as ``single`` /
+  ``batched``, b = (|a| + |c|)(1 + margin) (every row dominant by the
+  relative margin only; optionally every column as well), x* ~ U[-1, 1],
+  d = A x*.
 """
 from __future__ import annotations
 
@@ -119,6 +123,31 @@ def _values(seed: int, offsets: np.ndarray) -> System:
     x = uniform(seed, STREAM_X, n, -1.0, 1.0)
     d = matvec(a, b, c, x, offsets)
     return System(a, b, c, d, x, offsets.astype(np.int64))
+
+
+def weak(n: int = 0, margin: float = 1e-3, seed: int = 0, sizes=None, columns: bool = False) -> System:
+    """One system of n rows (or concatenated systems of the given sizes) in
+    which every row is diagonally dominant by the relative margin only:
+    b = (|a| + |c|)(1 + margin) with a, c ~ U[-1, 1] (zero at system ends).
+    With ``columns`` every column is dominant too (so is the transpose):
+    b_i = max(|a_i| + |c_i|, |c_{i-1}| + |a_{i+1}|)(1 + margin)."""
+    if sizes is None:
+        if n < 1:
+            raise ValueError("n must be >= 1")
+        sizes = [n]
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offsets = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    S = _values(seed, offsets)
+    row = np.abs(S.a) + np.abs(S.c)
+    if columns:
+        col = np.zeros_like(row)
+        col[1:] += np.abs(S.c[:-1])
+        col[:-1] += np.abs(S.a[1:])
+        row = np.maximum(row, col)
+    b = row * (1.0 + margin)
+    d = matvec(S.a, b, S.c, S.xstar, offsets)
+    return System(S.a, b, S.c, d, S.xstar, S.offsets)
 
 
 def single(n: int, seed: int = 0) -> System:
