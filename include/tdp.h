@@ -232,6 +232,13 @@ int tdp_status(void* stream);
  * the word this way. */
 int tdp_status_code(uint32_t bits);
 
+/* The raw device status word that the last checked-mode call or tdp_status
+ * call of this host thread read (before clearing it).  Besides the error bits
+ * above, bit 8 is informational: the windowed pass of a TDP_F32_REFINE solve
+ * found a tile whose checks failed and the exact binary64 fallback produced
+ * the answer (tdp_status_code maps it to TDP_OK). */
+uint32_t tdp_last_status_bits(void);
+
 /* Checked mode: when on, every solve synchronises its stream and returns the
  * device status.  Default off. */
 void tdp_set_checked(int on);

@@ -25,6 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 F64, F32, F32_REFINE = 0, 1, 2
 _ERRORS = {1: "EINVAL", 2: "ECUDA", 3: "ESINGULAR", 4: "ETIMEOUT", 5: "ENOMEM"}
 OK, EINVAL, ECUDA, ESINGULAR, ETIMEOUT, ENOMEM = range(6)
+ST_FALLBACK = 8  # status bit: the windowed pass fell back to the exact binary64 solve
 
 
 class TdpError(RuntimeError):
@@ -74,6 +75,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_solve_multi.argtypes = [P, P, P, P, P, I64, I32, I64, I64, I32, I32, P]
     lib.tdp_solve_host.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
     lib.tdp_status_code.argtypes = [ctypes.c_uint32]
+    lib.tdp_last_status_bits.restype = ctypes.c_uint32
     return lib
 
 
@@ -85,7 +87,7 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
            "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi", "tdp_solve_host",
-           "tdp_status_code")
+           "tdp_status_code", "tdp_last_status_bits")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP) = range(5)
 (TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S, TUNE_IFACE32, TUNE_REFINE_KEPT,

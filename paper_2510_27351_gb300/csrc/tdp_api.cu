@@ -21,6 +21,7 @@ namespace tdp {
 namespace {
 
 thread_local std::string g_last_error;
+thread_local unsigned g_last_bits = 0;  // raw status word of the last checked call or tdp_status
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_checked{0};
 
@@ -220,7 +221,8 @@ int run(void* stream, const char* fn, F&& driver) {
     e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string(fn) + ": " + cudaGetErrorString(e));
-    if (h) return status_error(h, fn);
+    g_last_bits = h;
+    if (status_code(h) != TDP_OK) return status_error(h, fn);
   }
   g_last_error.clear();
   return TDP_OK;
@@ -242,7 +244,7 @@ struct Row {
 std::mutex g_tab_mu;
 std::vector<Row> g_table;
 bool g_table_init = false;
-std::vector<float> g_feat[3];
+std::vector<double> g_feat[3];
 std::vector<int32_t> g_lab[3];
 
 void ensure_table() {
@@ -451,7 +453,7 @@ int load_rtable_file(const char* path) {
   return TDP_OK;
 }
 
-int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels) {
+int predictor_table(tdp_dtype dt, const double** feat, const int32_t** labels) {
   std::lock_guard<std::mutex> lk(g_tab_mu);
   ensure_table();
   auto& f = g_feat[int(dt)];
@@ -460,8 +462,8 @@ int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels) {
   l.clear();
   for (const Row& r : g_table) {
     if (r.dt != int(dt)) continue;
-    f.push_back(float(std::log2(r.n)));
-    f.push_back(float(std::log2(r.batch)));
+    f.push_back(std::log2(r.n));
+    f.push_back(std::log2(r.batch));
     l.push_back(r.s);
   }
   *feat = f.data();
@@ -688,7 +690,8 @@ int tdp_status(void* stream) {
   e = cudaMemcpy(&h, ws->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ws->status, 0, sizeof(unsigned));
   if (e != cudaSuccess) return set_error(TDP_ECUDA, std::string("tdp_status: ") + cudaGetErrorString(e));
-  return h ? status_error(h, "tdp_status") : TDP_OK;
+  g_last_bits = h;
+  return status_code(h) != TDP_OK ? status_error(h, "tdp_status") : TDP_OK;
 }
 
 void tdp_set_checked(int on) { g_checked.store(on ? 1 : 0); }
@@ -717,6 +720,8 @@ const char* tdp_last_error(void) { return g_last_error.c_str(); }
 int64_t tdp_launch_count(void) { return g_launches.load(); }
 
 int tdp_status_code(uint32_t bits) { return status_code(bits); }
+
+uint32_t tdp_last_status_bits(void) { return g_last_bits; }
 
 void tdp_profile_enable(int on) {
   profile_clear();

@@ -131,6 +131,6 @@ void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const voi
 void solve_multi(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n,
                  int32_t nrhs, int64_t ldd, int64_t ldx, int s, tdp_dtype dt);
 // Flattened table for the device-side predictor: rows of (log2 n, log2 batch, s) per dtype.
-int predictor_table(tdp_dtype dt, const float** feat, const int32_t** labels);
+int predictor_table(tdp_dtype dt, const double** feat, const int32_t** labels);
 
 }  // namespace tdp

@@ -103,7 +103,7 @@ extern "C" int tdp_solve_noalloc(const void* a, const void* b, const void* c, co
     unsigned h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(TDP_ECUDA, std::string("tdp_solve_noalloc: ") + cudaGetErrorString(e));
-    if (h) return status_error(h, "tdp_solve_noalloc");
+    if (status_code(h) != TDP_OK) return status_error(h, "tdp_solve_noalloc");
   }
   return set_last_error(TDP_OK, "");
 }

@@ -20,6 +20,7 @@
 #include "tdp_refine.cuh"
 #include "tdp_const.cuh"
 #include "tdp_multi.cuh"
+#include "tdp_window.cuh"
 
 namespace tdp {
 
@@ -225,11 +226,12 @@ void stage3_resolve(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, in
 // ---------------------------------------------------------------------------
 constexpr int64_t kCoopMax = int64_t(1) << 19;  // interface systems at most this large go to one launch
 
-// All remaining recursion levels of an interface system of M rows in one
-// cooperative launch (k_iface_coop).
-void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
-                          double* y, int64_t M) {
-  CoopParams P{};
+// Levels of the one-launch interface solve for a system of M rows (ra .. rd,
+// solution y): workspace taken from ctx's arena, parameters in P (P.L = 0
+// when M <= kBaseRows: no level, the system goes to one warp).
+void coop_build(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd, double* y,
+                int64_t M, CoopParams& P) {
+  P = CoopParams{};
   int L = 0;
   const double *a = ra, *b = rb, *c = rc, *d = rd;
   double* yl = y;
@@ -259,15 +261,41 @@ void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const do
   P.bar_extra = ctx.wait_never ? 1u : 0u;
   P.base_scratch = ctx.ar->take<double>(Ml);
   P.ybase = (L > 0) ? ctx.ar->take<double>(Ml) : y;
+}
+
+// Grid of a cooperative launch: co-resident CTAs of `threads` threads, at
+// most `want`.
+template <typename K>
+int coop_grid(K kernel, int threads, int64_t want) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> per_sm_of;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    auto it = per_sm_of.find(key);
+    if (it == per_sm_of.end()) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) per_sm = 0;
+      per_sm_of[key] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
+  }
+  return int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(per_sm, 1)) * sm_count())));
+}
+
+// All remaining recursion levels of an interface system of M rows in one
+// cooperative launch (k_iface_coop).
+void solve_interface_coop(Ctx& ctx, const double* ra, const double* rb, const double* rc, const double* rd,
+                          double* y, int64_t M) {
+  CoopParams P;
+  coop_build(ctx, ra, rb, rc, rd, y, M, P);
   unsigned* bar = ctx.ar->take<unsigned>(2);
   if (ctx.dry || ctx.err != cudaSuccess) return;
   ctx.fail(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), ctx.stream), "barrier clear");
-  static int per_sm = -1;
-  if (per_sm < 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iface_coop, 128, 0) != cudaSuccess) per_sm = 0;
-  }
-  const int64_t want = std::max<int64_t>(1, (P.lv[0].m + 127) / 128);
-  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(per_sm, 1)) * sm_count())));
+  const int grid = coop_grid(k_iface_coop, 128, (P.lv[0].m + 127) / 128);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);
@@ -496,13 +524,22 @@ struct KpTable {
   int32_t lab[kKpMax];
 };
 
+// log2 of a positive value as its binary exponent plus log2 of its
+// mantissa: exact for powers of two (as the host's features are), so that
+// equal distances, and with them the tie rule, come out as on the host.
+__device__ __forceinline__ double log2_split(double v) {
+  int e;
+  const double m = frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
+  return double(e - 1) + log2(2.0 * m);
+}
+
 __global__ void k_predict_sizes(const int64_t* __restrict__ off, int32_t batch, const __grid_constant__ KpTable tab,
                                 int fallback, int clamp, int32_t* __restrict__ s_out) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= batch) return;
   int64_t n = off[j + 1] - off[j];
   if (n < 1) n = 1;
-  const double ln = log2(double(n)), lb = log2(double(batch));
+  const double ln = log2_split(double(n)), lb = log2_split(double(batch));
   double best = 1e300;
   int s = 0;
   for (int r = 0; r < tab.rows; ++r) {
@@ -629,6 +666,70 @@ __global__ void k_scatter(const S* __restrict__ src, S* __restrict__ dst, int32_
 unsigned grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
+}
+
+// Offsets of a batch solved as one system: offsets[0] = 0, non-decreasing,
+// offsets[batch] = total_n; anything else raises ST_BADARG.
+__global__ void k_check_offsets(const int64_t* __restrict__ off, int32_t batch, int64_t total_n,
+                                unsigned* __restrict__ status) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j <= batch;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t v = off[j];
+    if ((j == 0 && v != 0) || (j == batch && v != total_n) || (j > 0 && off[j - 1] > v)) flag(status, ST_BADARG);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Binary32 solve with binary64 refinement in one windowed pass
+// (tdp_window.cuh), followed by the exact binary64 solve of the whole system
+// in one cooperative launch that runs only when a tile failed its checks.
+// off: a batch solved as one system (nsys systems), null for one system.
+// ---------------------------------------------------------------------------
+constexpr int kWinSW = 7;  // window rows per thread
+
+void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, const double* d, double* x,
+                   int64_t n, int iters, const int64_t* off, int32_t nsys) {
+  const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~1;
+  const int TR = kWinT * kWinSW - 2 * H;
+  const int64_t tiles = (n + TR - 1) / TR;
+  unsigned* gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
+  const int64_t m0 = (n + kExS - 1) / kExS;
+  ExactParams E{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
+  E.ra = ctx.ar->take<double>(2 * m0);
+  E.rb = ctx.ar->take<double>(2 * m0);
+  E.rc = ctx.ar->take<double>(2 * m0);
+  E.rd = ctx.ar->take<double>(2 * m0);
+  E.y0 = ctx.ar->take<double>(2 * m0);
+  CoopParams P;
+  coop_build(ctx, E.ra, E.rb, E.rc, E.rd, E.y0, 2 * m0, P);
+  if (ctx.dry || ctx.err != cudaSuccess) return;
+  ctx.fail(cudaMemsetAsync(gate, 0, 3 * sizeof(unsigned), ctx.stream), "gate clear");
+  if (off) {
+    pre_launch(ctx, "check_offsets");
+    k_check_offsets<<<grid_for(int64_t(nsys) + 1, 256), 256, 0, ctx.stream>>>(off, nsys, n, ctx.status);
+    post_launch(ctx, "offsets check");
+  }
+  WinParams W{a, b, c, d, x, n, H, TR, iters, off, nsys, gate, ctx.status};
+  auto wk = k_window_refine<kWinSW>;
+  allow_smem(wk);
+  pre_launch(ctx, "window_refine");
+  wk<<<unsigned(tiles), kWinT, WinSmem<kWinSW>::bytes(), ctx.stream>>>(W);
+  post_launch(ctx, "windowed pass");
+  const int grid = coop_grid(k_exact_coop, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  pre_launch(ctx, "exact_fallback");
+  ctx.fail(cudaLaunchKernelEx(&cfg, k_exact_coop, E, P, (const unsigned*)gate, gate + 1, ctx.status),
+           "exact fallback launch");
+  post_launch(ctx, "exact fallback");
 }
 
 // ---------------------------------------------------------------------------
@@ -785,7 +886,7 @@ struct SizeModel {
 };
 
 bool size_model(tdp_dtype dt, int32_t batch, SizeModel* sm) {
-  const float* feat = nullptr;
+  const double* feat = nullptr;
   const int32_t* lab = nullptr;
   const int rows = std::min(predictor_table(dt, &feat, &lab), kKpMax);
   if (rows <= 0) return false;
@@ -1013,6 +1114,11 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
   ctx.rec_n = n;
   ctx.rec_batch = 1;
   ctx.rec_dt = dt;
+  if (dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0) {
+    window_refine(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, n,
+                  refine_iters, nullptr, 0);
+    return;
+  }
   if (s > n) s = int(std::max<int64_t>(2, n));
   const int64_t m = (n + s - 1) / s;
   solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
@@ -1230,6 +1336,12 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
   ctx.rec_batch = batch;
   ctx.rec_dt = dt;
   if (batch <= 0 || total_n <= 0) return;
+  if (dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0 && !ctx.per_system_s) {
+    // every batch as one system: the windowed pass cuts the couplings between systems
+    window_refine(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, total_n,
+                  refine_iters, offsets, batch);
+    return;
+  }
   const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;
   if (s == 0) {
     // per-system sizes from the device predictor (TDP_PER_SYSTEM_S=1); the

@@ -1,0 +1,204 @@
+"""The windowed single pass of TDP_F32_REFINE against the oracle, through the C ABI.
+
+The pass solves every tile of rows inside a window with halo rows on both
+sides (binary32 eliminations, binary64 residual and corrections, one read of
+the inputs) and checks, per tile, that the window's rows are diagonally
+dominant and that the decay of A^-1 across the halo bounds the windowed
+solution's distance from x by 2^-45 ||x||_inf.  A tile that fails sets the
+fallback bit of the status word and the exact binary64 solve answers.
+
+Tolerances (relative infinity norm against the oracle's binary64 Thomas):
+1e-12 with at least one correction, 1e-5 without (the binary32 solve alone).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tdp():
+    import torch
+
+    import paper_2510_27351_gb300 as tdp
+
+    assert torch.cuda.is_available()
+    tdp.tdp_set_checked(True)
+    assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW) == 1
+    yield tdp
+    tdp.tdp_set_checked(False)
+
+
+def dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def per_system_err(x, ref, offsets):
+    worst = 0.0
+    for j in range(len(offsets) - 1):
+        lo, hi = int(offsets[j]), int(offsets[j + 1])
+        if hi > lo:
+            worst = max(worst, oracle.rel_err(x[lo:hi], ref[lo:hi]))
+    return worst
+
+
+def solve(tdp, a, b, c, d, n, iters):
+    import torch
+
+    A, B, C, D = (dev(v) for v in (a, b, c, d))
+    x = torch.full_like(D, float("nan"))
+    tdp.tdp_solve(A, B, C, D, x, n, 0, tdp.F32_REFINE, iters)
+    torch.cuda.synchronize()
+    return host(x), tdp.LIB.tdp_last_status_bits()
+
+
+TILE = 256 * 7 - 2 * 48  # owned rows per tile at the default halo
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2])
+def test_window_single_sizes(tdp, iters):
+    """Sizes around tile boundaries, one row, odd ends; every tile passes."""
+    tol = 1e-5 if iters == 0 else 1e-12
+    for n in (1, 2, 3, 5, 47, 48, 49, 97, TILE - 1, TILE, TILE + 1, 2 * TILE + 3, 100_003, (1 << 20) + 1):
+        S = W.single(n, seed=n + 13)
+        ref = oracle.thomas(S.a, S.b, S.c, S.d)
+        x, bits = solve(tdp, S.a, S.b, S.c, S.d, n, iters)
+        assert np.all(np.isfinite(x)), n
+        assert not bits & tdp.ST_FALLBACK, n
+        e = oracle.rel_err(x, ref)
+        assert e <= tol, (n, iters, e)
+
+
+def test_window_matches_exact_schedule(tdp):
+    """The windowed pass and the exact three-pass schedule (TDP_TUNE_WINDOW =
+    0) agree with each other and with x* to the refinement's accuracy."""
+    import torch
+
+    n = 3_000_017
+    S = W.single(n, seed=5)
+    ref = oracle.thomas(S.a, S.b, S.c, S.d)
+    xw, bits = solve(tdp, S.a, S.b, S.c, S.d, n, 1)
+    assert not bits & tdp.ST_FALLBACK
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 0)
+    try:
+        A, B, C, D = (dev(v) for v in (S.a, S.b, S.c, S.d))
+        x3 = torch.empty_like(D)
+        tdp.tdp_solve(A, B, C, D, x3, n, 24, tdp.F32_REFINE, 1)
+        torch.cuda.synchronize()
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 1)
+    assert oracle.rel_err(xw, ref) <= 1e-12
+    assert oracle.rel_err(host(x3), ref) <= 1e-12
+    assert oracle.rel_err(xw, S.xstar) <= 1e-12
+
+
+def test_window_batches(tdp):
+    """Batches solved as one system through the windowed pass: log-uniform
+    sizes, and tiny, one-row and empty systems (cut points inside windows and
+    halos); every system against the oracle on its own."""
+    import torch
+
+    for Sb in (W.batched(256, 64, 65536, seed=3), W.batched(sizes=[0, 1, 2, 3, 0, 5, 64, 1, 1700, 47, 48, 0],
+                                                            seed=4),
+               W.batched(3000, 2, 200, seed=6)):
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        A, B, C, D = (dev(v) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+        for iters in (1, 2):
+            x = torch.full_like(D, float("nan"))
+            tdp.tdp_solve_batched(dev(Sb.offsets), Sb.batch, Sb.n, A, B, C, D, x, 0, tdp.F32_REFINE, iters)
+            torch.cuda.synchronize()
+            assert not tdp.LIB.tdp_last_status_bits() & tdp.ST_FALLBACK
+            e = per_system_err(host(x), ref, Sb.offsets)
+            assert e <= 1e-12, (Sb.batch, iters, e)
+
+
+def test_window_bad_offsets(tdp):
+    import torch
+
+    Sb = W.batched(sizes=[10, 20], seed=1)
+    A, B, C, D = (dev(v) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+    x = torch.empty_like(D)
+    for bad in ([0, 20, 10], [1, 10, 30], [0, 10, 29]):
+        with pytest.raises(tdp.TdpError) as ei:
+            tdp.tdp_solve_batched(dev(np.array(bad, dtype=np.int64)), 2, 30, A, B, C, D, x, 0, tdp.F32_REFINE, 1)
+        assert ei.value.code == tdp.EINVAL
+
+
+def test_window_heat_step_passes_its_bound(tdp):
+    """tdp(-r, 1 + 2r, -r) at r = 0.5: every factor of the decay bound is
+    1/2, and 48 halo rows give 2^-48 < 2^-46, so the windowed pass answers."""
+    n = 1 << 20
+    r = 0.5
+    a = np.full(n, -r)
+    b = np.full(n, 1 + 2 * r)
+    c = np.full(n, -r)
+    d = W.uniform(9, 5, n, 0.0, 1.0)
+    ref = oracle.thomas(a, b, c, d)
+    x, bits = solve(tdp, a, b, c, d, n, 1)
+    assert not bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, ref) <= 1e-12
+
+
+def test_window_falls_back_on_a_weak_region(tdp):
+    """A strongly dominant system with one nearly weakly dominant stretch of
+    5000 rows: the tiles around it fail the decay bound, the exact binary64
+    solve answers (fallback bit set), and the answer matches the oracle.
+    A shorter halo (16 rows) fails the bound on ordinary tiles as well."""
+    n = 1_000_003
+    S = W.single(n, seed=17)
+    a, c = S.a.copy(), S.c.copy()
+    b = S.b.copy()
+    lo, hi = 500_000, 505_000
+    b[lo:hi] = (np.abs(a[lo:hi]) + np.abs(c[lo:hi])) * (1 + 1e-3)
+    d = W.matvec(a, b, c, S.xstar, S.offsets)
+    ref = oracle.thomas(a, b, c, d)
+    x, bits = solve(tdp, a, b, c, d, n, 1)
+    assert bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, ref) <= 1e-12
+    # an input that is not diagonally dominant at all: fallback, still exact (binary64)
+    b2 = S.b.copy()
+    b2[123_456] = 0.25  # |a| + |c| may exceed b here
+    d2 = W.matvec(S.a, b2, S.c, S.xstar, S.offsets)
+    ref2 = oracle.thomas(S.a, b2, S.c, d2)
+    x2, bits2 = solve(tdp, S.a, b2, S.c, d2, n, 1)
+    if abs(S.a[123_456]) + abs(S.c[123_456]) > 0.25:
+        assert bits2 & tdp.ST_FALLBACK
+    assert oracle.rel_err(x2, ref2) <= 1e-12
+    old = tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO)
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, 16)
+    try:
+        x3, _ = solve(tdp, S.a, S.b, S.c, S.d, n, 1)
+        assert oracle.rel_err(x3, oracle.thomas(S.a, S.b, S.c, S.d)) <= 1e-12
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, old)
+
+
+def test_window_fallback_timeout_reported(tdp):
+    """The fallback's grid barrier made unreachable (testing key): its wait
+    runs out and the call reports TDP_ETIMEOUT; with the gate clear the
+    fallback returns at once and never waits."""
+    n = 200_003
+    S = W.weak(n, 1e-3, seed=2)
+    G = W.single(n, seed=2)
+    old = (tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER), tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2))
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 14)
+    tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, 1)
+    try:
+        with pytest.raises(tdp.TdpError) as ei:
+            solve(tdp, S.a, S.b, S.c, S.d, n, 1)
+        assert ei.value.code == tdp.ETIMEOUT
+        x, bits = solve(tdp, G.a, G.b, G.c, G.d, n, 1)  # every tile passes: no barrier is reached
+        assert not bits & tdp.ST_FALLBACK
+        assert oracle.rel_err(x, oracle.thomas(G.a, G.b, G.c, G.d)) <= 1e-12
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
+        tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
