@@ -2,14 +2,15 @@
 """Throughput of the GB300 tridiagonal partition solver.
 
 Default workload: one system of N = 2^26 unknowns, binary64 storage, the
-benchmark distribution (b ~ U[4,8], a, c ~ U[-1,1], x* ~ U[-1,1], d = A x*),
-sub-system size from the predictor.  A timed step is one binary64 solve
-(predictor lookup, Stage 1, the recursive interface solve, Stage 3) of that
-system with inputs resident in HBM; the inputs (2 GiB) exceed L2.  The same
-run also times the binary32 + binary64-refinement solve, binary32 storage,
-the plain one-thread-per-system GPU Thomas baseline, the 4096-system batched
-workload, the adjoint workload and the implicit heat step, and reports them
-under "variants".
+benchmark distribution (b ~ U[4,8], a, c ~ U[-1,1], x* ~ U[-1,1], d = A x*).
+A timed step is one solve of that system to binary64 accuracy with inputs
+resident in HBM (2 GiB, larger than L2): the headline is the binary32 solve
+with one binary64 refinement step (the windowed single pass; error about
+1e-13 against x*), and the plain binary64 solve (predictor lookup, Stage 1,
+the recursive interface solve, Stage 3) is timed the same way under "fp64".
+The same run also times binary32 storage, the plain one-thread-per-system GPU
+Thomas baseline, the 4096-system batched workload, the adjoint workload and
+the implicit heat step, and reports them under "variants".
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
 replica (independent problems, no collective on the data path).
@@ -36,11 +37,12 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 N_MAIN = 1 << 26
-METRIC = "unknowns solved/sec (FP64 partition solve, N=2^26)"
-WORKLOAD = "single tridiagonal system N=2^26, binary64, b~U[4,8], a,c~U[-1,1], d=A x*"
+METRIC = "unknowns solved/sec (N=2^26 to binary64 accuracy: FP32 solve + FP64 refinement; FP64 solve beside it)"
+WORKLOAD = "single tridiagonal system N=2^26, binary64 storage, b~U[4,8], a,c~U[-1,1], d=A x*"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # binary64 pipe: 2 operations (FMA or MUL) per clock per SM, the nominal
-# 1.25 TFLOP/s over 152 SMs at 2.07 GHz with 2 flops per FMA
+# 1.25 TFLOP/s over 152 SMs at 2.07 GHz with 2 flops per FMA; the roofline
+# uses the rate measured in the same run (tdp_fp64_fma_rate) when it can
 FP64_PEAK_GOPS = 152 * 2.07e9 * 2 / 1e9
 FP64_PEAK_TFLOPS = FP64_PEAK_GOPS * 2 / 1e3
 
@@ -56,22 +58,47 @@ def stage1_f64_ops(s):
     return fma, mul
 
 
-def stage1_f64_roofline(ms, n, s, hbm_peak_gbs, traffic=None):
+def stage1_f64_roofline(ms, n, s, hbm_peak_gbs, traffic=None, peak_gops=None, peak_source=None):
     """ALU roofline of the binary64 Stage 1 from its event-timed launch (ms):
-    binary64 pipe operations per second against the pipe's 2 per clock per
-    SM, and the same work in flops against the FMA-only flop peak."""
+    binary64 pipe operations per second against the pipe's rate (measured in
+    this run when given, else the derived 2 per clock per SM), and the same
+    work in flops against the FMA-only flop peak."""
     fma, mul = stage1_f64_ops(s)
     ops = (fma + mul) * n / s
     flops = (2 * fma + mul) * n / s
     gops = ops / (ms * 1e-3) / 1e9
     tflops = flops / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": gops, "peak": FP64_PEAK_GOPS,
-            "unit": "Gop/s", "frac": gops / FP64_PEAK_GOPS, "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA or MUL per clock",
-            "ops_per_row": (fma + mul) / s, "fma_mul_per_block": [fma, mul],
-            "achieved_tflops": tflops, "peak_tflops": FP64_PEAK_TFLOPS, "frac_flops": tflops / FP64_PEAK_TFLOPS,
+    peak = peak_gops or FP64_PEAK_GOPS
+    return {"bound": "alu", "kernel": "stage1_keep_f64", "achieved": gops, "peak": peak,
+            "unit": "Gop/s", "frac": gops / peak, "traffic": traffic,
+            "peak_source": peak_source or "derived: 152 SMs x 2.07 GHz x 2 binary64 FMA or MUL per clock",
+            "peak_derived": FP64_PEAK_GOPS, "ops_per_row": (fma + mul) / s, "fma_mul_per_block": [fma, mul],
+            "achieved_tflops": tflops, "peak_tflops": 2 * peak / 1e3, "frac_flops": tflops / (2 * peak / 1e3),
             "algorithmic_bytes_per_row": 56 + 64 / s,
             "hbm_frac_of_kernel": (56 + 64 / s) * n / (ms * 1e-3) / 1e9 / hbm_peak_gbs}
+
+
+def window_geometry(tdp):
+    """(rows per thread, halo rows, owned rows per tile) of the windowed pass."""
+    sw = tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW)
+    halo = max(16, min(tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO), 64)) & ~1
+    return sw, halo, 256 * sw - 2 * halo
+
+
+def window_roofline(tdp, ms, n, iters, hbm_peak_gbs, fp64_peak_gops, traffic=None):
+    """HBM roofline of the windowed pass (k_window_refine) from its event-timed
+    launch: 32 bytes read and 8 written per row (algorithmic), against the
+    measured copy bandwidth; beside it the binary64 pipe: per correction
+    3 FMA per window row (the residual) and 1 add per owned row (the update)."""
+    sw, halo, tr = window_geometry(tdp)
+    gbs = 40 * n / (ms * 1e-3) / 1e9
+    ops_row = iters * (3 * (256 * sw) / tr + 1)
+    gops = ops_row * n / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "window_refine", "achieved": gbs, "peak": hbm_peak_gbs, "unit": "GB/s",
+            "frac": gbs / hbm_peak_gbs, "traffic": traffic, "algorithmic_bytes_per_row": 40,
+            "geometry": {"rows_per_thread": sw, "halo": halo, "tile_rows": tr, "window_rows": 256 * sw},
+            "fp64_ops_per_row": ops_row, "fp64_achieved_gops": gops, "fp64_peak_gops": fp64_peak_gops,
+            "fp64_frac": gops / fp64_peak_gops}
 
 
 def log(*a):
@@ -240,7 +267,8 @@ def _reference_line(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_MAIN, "batch": 1},
-        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_info()[0], "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -326,65 +354,97 @@ def run_ours(args, world, rank, local):
     x = torch.empty(N_MAIN, dtype=torch.float64, device=device)
     torch.cuda.synchronize()
     s_main = tdp.tdp_predict_s(N_MAIN, 1, tdp.F64)
+    fp64_rate, fp64_ms = tdp.tdp_fp64_fma_rate(stream)
+    fp64_peak = fp64_rate / 1e9
+    fp64_src = f"measured in this run: tdp_fp64_fma_rate, {fp64_rate:.4g} binary64 FMA/s ({fp64_ms:.2f} ms launch)"
 
     def step_f64():
         s = tdp.tdp_predict_s(N_MAIN, 1, tdp.F64)
         tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, s, tdp.F64, 0, stream)
 
-    # correctness guard on the timed configuration (vs x*)
-    step_f64()
-    torch.cuda.synchronize()
-    err_xstar = float((x.cpu().numpy() - S.xstar).__abs__().max() / np.abs(S.xstar).max())
+    def step_refine():
+        tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, 0, tdp.F32_REFINE, 1, stream)
 
-    launches0 = tdp.tdp_launch_count()
-    with ClockSampler(local) as clk:
-        for _ in range(args.warmup):
-            step_f64()
+    def check(step):
+        """Error against x* of the timed configuration, and the status bits
+        (a set fallback bit would mean the exact solve answered instead)."""
+        tdp.tdp_set_checked(True)
+        step()
+        bits = int(tdp.LIB.tdp_last_status_bits())
+        tdp.tdp_set_checked(False)
         torch.cuda.synchronize()
-        barrier_max(0.0, world, device)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        launches_a = tdp.tdp_launch_count()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step_f64()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        launches_b = tdp.tdp_launch_count()
-        ms = e0.elapsed_time(e1) / args.steps
-        # keep the same load (untimed) for a moment so that the clock samples
-        # cover at least half a second of it
-        t_end = time.time() + 0.6
-        while time.time() < t_end:
-            for _ in range(20):
-                step_f64()
+        return float((x.cpu().numpy() - S.xstar).__abs__().max() / np.abs(S.xstar).max()), bits
+
+    def timed(step):
+        """ms per step over args.steps steps after args.warmup, the max over
+        ranks, with the clocks sampled during the load and our launches counted."""
+        with ClockSampler(local) as clk:
+            for _ in range(args.warmup):
+                step()
             torch.cuda.synchronize()
-    ms = barrier_max(ms, world, device)
-    clocks = clk.summary()
-    value = weak_value(N_MAIN, world, ms)
-    gpu_launches = launches_b - launches_a
+            barrier_max(0.0, world, device)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            la = tdp.tdp_launch_count()
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lb = tdp.tdp_launch_count()
+            ms_ = e0.elapsed_time(e1) / args.steps
+            # keep the same load (untimed) for a moment so that the clock
+            # samples cover at least half a second of it
+            t_end = time.time() + 0.6
+            while time.time() < t_end:
+                for _ in range(20):
+                    step()
+                torch.cuda.synchronize()
+        return barrier_max(ms_, world, device), clk.summary(), lb - la
 
-    # ---- roofline of the dominant kernel (library event timing of the same step) ----
-    prof = profile_kernels(tdp, step_f64, max(3, min(args.steps, 10)))
+    # ---- headline: binary32 solve + one binary64 correction (windowed pass) ----
+    err_refine, bits_refine = check(step_refine)
+    ms, clocks, gpu_launches = timed(step_refine)
+    value = weak_value(N_MAIN, world, ms)
+    prof = profile_kernels(tdp, step_refine, max(3, min(args.steps, 10)))
     dom = max(prof.items(), key=lambda kv: kv[1][0] * kv[1][1])  # largest total time per step
-    st1 = prof.get("stage1_keep_f64")
+    win = prof.get("window_refine")
     roof = None
-    if st1:
-        roof = stage1_f64_roofline(st1[1], N_MAIN, s_main, hbm_peak,
-                                   measured_traffic("stage1_keep_f64", s_main, N_MAIN))
+    if win:
+        roof = window_roofline(tdp, win[1], N_MAIN, 1, hbm_peak, fp64_peak,
+                               measured_traffic("window_refine", window_geometry(tdp)[0], N_MAIN))
     solve_hbm_frac = value / world * 40 / 1e9 / hbm_peak
+
+    # ---- the binary64 solve of the same system ----
+    err_xstar, _ = check(step_f64)
+    ms64, clocks64, launches64 = timed(step_f64)
+    prof64 = profile_kernels(tdp, step_f64, max(3, min(args.steps, 10)))
+    st1 = prof64.get("stage1_keep_f64")
+    roof64 = None
+    if st1:
+        roof64 = stage1_f64_roofline(st1[1], N_MAIN, s_main, hbm_peak,
+                                     measured_traffic("stage1_keep_f64", s_main, N_MAIN), fp64_peak, fp64_src)
+    fp64 = {"value": weak_value(N_MAIN, world, ms64), "unit": "unknowns/s", "ms_per_step": ms64, "s": s_main,
+            "hbm_frac_40B": weak_value(N_MAIN, world, ms64) / world * 40 / 1e9 / hbm_peak,
+            "rel_err_vs_xstar": err_xstar, "roofline": roof64, "kernels_ms": {k: v[1] for k, v in prof64.items()},
+            "gpu_launches": launches64, "clocks": clocks64}
 
     # ---- end to end through the public API with host buffers ----
     host_x = torch.empty(N_MAIN, dtype=torch.float64).pin_memory()
 
     def step_e2e():
-        # the library's host-array entry: copies in, solve, copy out, pipelined
+        # the library's host-array entry: copies in, solve, copy out
+        tdp.tdp_solve_host(host["a"], host["b"], host["c"], host["d"], host_x, N_MAIN, 0, tdp.F32_REFINE, 1, stream)
+
+    def step_e2e64():
+        # binary64: the copies pipelined with Stage 1 and Stage 3
         tdp.tdp_solve_host(host["a"], host["b"], host["c"], host["d"], host_x, N_MAIN, s_main, tdp.F64, 0, stream)
 
-    e2e_ms = cuda_time(step_e2e, max(3, args.steps // 2), 2, stream)
-    e2e_ms = barrier_max(e2e_ms, world, device)
+    e2e_ms = barrier_max(cuda_time(step_e2e, max(3, args.steps // 2), 2, stream), world, device)
+    e2e64_ms = barrier_max(cuda_time(step_e2e64, max(3, args.steps // 2), 2, stream), world, device)
     e2e = {"value": world * N_MAIN / (e2e_ms * 1e-3), "unit": "unknowns/s", "h2d_bytes_per_step": 4 * 8 * N_MAIN,
-           "d2h_bytes_per_step": 8 * N_MAIN, "ms_per_step": e2e_ms}
+           "d2h_bytes_per_step": 8 * N_MAIN, "ms_per_step": e2e_ms,
+           "fp64": {"value": world * N_MAIN / (e2e64_ms * 1e-3), "ms_per_step": e2e64_ms}}
 
     variants = {}
     if not args.main_only:
@@ -392,19 +452,20 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(S)
+        cpu = cpu_baseline(S, W.batched(4096, 64, 65536, seed=0))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_MAIN, "batch": 1, "s": s_main, "parallelism": f"replicas{world}",
-                       "l2": "inputs (2 GiB) larger than L2; no flush"},
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_MAIN, "batch": 1, "refine_iters": 1,
+                       "parallelism": f"replicas{world}", "l2": "inputs (2 GiB) larger than L2; no flush"},
             "roofline": roof, "hbm_frac_of_whole_solve": solve_hbm_frac, "peaks_source": pk_src,
-            "hbm_peak_gbs": hbm_peak, "kernels_ms": {k: v[1] for k, v in prof.items()},
-            "dominant_kernel": dom[0], "rel_err_vs_xstar": err_xstar, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clocks, "cpu_baseline": cpu, "variants": variants,
+            "hbm_peak_gbs": hbm_peak, "fp64_peak": {"gops": fp64_peak, "source": fp64_src},
+            "kernels_ms": {k: v[1] for k, v in prof.items()}, "dominant_kernel": dom[0],
+            "rel_err_vs_xstar": err_refine, "status_bits": bits_refine, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks, "fp64": fp64, "cpu_baseline": cpu, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -413,18 +474,84 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
-def cpu_baseline(S):
-    import oracle
+def cpu_info():
+    """(CPU model string, usable host cores) of this machine."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
 
-    t_end = time.perf_counter() + 10.0
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return model or platform.machine(), cores
+
+
+def _timed_reps(fn, seconds):
+    t_end = time.perf_counter() + seconds
     reps, t = 0, 0.0
     while time.perf_counter() < t_end or reps == 0:
         t0 = time.perf_counter()
-        oracle.thomas(S.a, S.b, S.c, S.d)
+        fn()
         t += time.perf_counter() - t0
         reps += 1
-    return {"value": reps * N_MAIN / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle Thomas (binary64) on the full N=2^26 system, {reps} repetitions (~10 s)"}
+    return reps, t
+
+
+def cpu_baseline(S, Sb=None):
+    """The oracle's binary64 Thomas on the host: one core on the whole
+    N = 2^26 system, and every host core at once (a thread per core; the
+    oracle's C code runs outside the interpreter lock) on equal slices of it
+    solved as independent systems (a throughput figure for the same rows, not
+    the same solve) and on the systems of the 4096-system batch."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    model, cores = cpu_info()
+    reps, t = _timed_reps(lambda: oracle.thomas(S.a, S.b, S.c, S.d), 8.0)
+    one = {"value": reps * N_MAIN / t, "cores": 1,
+           "sample": f"oracle Thomas on the full N=2^26 system, {reps} repetitions (~8 s)"}
+    bounds = np.linspace(0, N_MAIN, cores + 1).astype(np.int64)
+    slices = [(int(lo), int(hi)) for lo, hi in zip(bounds[:-1], bounds[1:])]
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        def all_slices():
+            list(ex.map(lambda r: oracle.thomas(S.a[r[0]:r[1]], S.b[r[0]:r[1]], S.c[r[0]:r[1]], S.d[r[0]:r[1]]),
+                        slices))
+
+        reps_m, t_m = _timed_reps(all_slices, 8.0)
+        batched = None
+        if Sb is not None:
+            groups = np.array_split(np.arange(Sb.batch), cores)
+
+            def one_group(g):
+                lo, hi = int(Sb.offsets[g[0]]), int(Sb.offsets[g[-1] + 1])
+                oracle.thomas_batched(Sb.a[lo:hi], Sb.b[lo:hi], Sb.c[lo:hi], Sb.d[lo:hi],
+                                      offsets=Sb.offsets[g[0]:g[-1] + 2] - lo)
+
+            reps_b, t_b = _timed_reps(lambda: list(ex.map(one_group, [g for g in groups if len(g)])), 5.0)
+            batched = {"value": reps_b * Sb.n / t_b, "cores": cores,
+                       "sample": f"oracle Thomas per system, 4096-system batch (sum N = {Sb.n}), {reps_b} passes"}
+    return {"value": reps_m * N_MAIN / t_m, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle Thomas on {cores} equal slices of the N=2^26 rows, one thread each, "
+                      f"{reps_m} passes (~8 s)",
+            "cpu_model": model, "nproc": os.cpu_count(), "one_core": one, "batched_4096": batched}
 
 
 def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
@@ -437,16 +564,24 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
     def hbm(ms, bytes_):
         return bytes_ / (ms * 1e-3) / 1e9 / hbm_peak
 
-    # binary32 + binary64 refinement on the same system (binary64 storage)
+    # binary32 + binary64 refinement on the same system by the exact three-pass
+    # schedule (the windowed pass off): the path the windowed pass falls back on
+    # in spirit, and the previous default
     s_r = tdp.tdp_predict_s(N_MAIN, 1, tdp.F32_REFINE)
-    fn = lambda: tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, s_r, tdp.F32_REFINE, 1, stream)
-    ms = cuda_time(fn, steps, 2, stream)
-    fn()
-    torch.cuda.synchronize()
-    err = float(np.abs(x.cpu().numpy() - S.xstar).max() / np.abs(S.xstar).max())
-    prof = profile_kernels(tdp, fn, 3)
-    out["fp32_refine1"] = {"ms": ms, "unknowns_per_s": N_MAIN / (ms * 1e-3), "hbm_frac_40B": hbm(ms, 40 * N_MAIN),
-                           "s": s_r, "rel_err_vs_xstar": err, "kernels_ms": {k: v[1] for k, v in prof.items()}}
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 0)
+    try:
+        fn = lambda: tdp.tdp_solve(dev["a"], dev["b"], dev["c"], dev["d"], x, N_MAIN, s_r, tdp.F32_REFINE, 1,
+                                   stream)
+        ms = cuda_time(fn, steps, 2, stream)
+        fn()
+        torch.cuda.synchronize()
+        err = float(np.abs(x.cpu().numpy() - S.xstar).max() / np.abs(S.xstar).max())
+        prof = profile_kernels(tdp, fn, 3)
+    finally:
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 1)
+    out["fp32_refine1_three_pass"] = {"ms": ms, "unknowns_per_s": N_MAIN / (ms * 1e-3),
+                                      "hbm_frac_40B": hbm(ms, 40 * N_MAIN), "s": s_r, "rel_err_vs_xstar": err,
+                                      "kernels_ms": {k: v[1] for k, v in prof.items()}}
     # binary32 storage
     s_f = tdp.tdp_predict_s(N_MAIN, 1, tdp.F32)
     d32 = {k: v.float() for k, v in dev.items()}

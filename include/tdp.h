@@ -285,8 +285,19 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_WAIT_LOG2 22   /* every bounded device wait gives up after 2^value clock cycles [10, 40] */
 #define TDP_TUNE_WAIT_NEVER 23  /* 1 (testing only): grid barriers wait for one arrival more than the grid has,
                                    so every such wait runs out and the call reports TDP_ETIMEOUT */
+#define TDP_TUNE_WINDOW_SW 24   /* rows per thread in the windowed pass's window: 5 or 7 (odd, so that the
+                                   threads' strided shared-memory reads avoid bank conflicts) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
+
+/* Measured binary64 FMA rate of the current device (a diagnostic, not part
+ * of the method): every thread of four full waves of CTAs runs 8 independent
+ * chains of 2048 dependent FMAs.  *fma_per_s receives FMAs per second of the
+ * fastest of three timed launches (after one warm-up launch), *ms_out (may be
+ * NULL) that launch's duration.  This is the denominator of the binary64
+ * kernels' ALU roofline.  Synchronises `stream`; allocates and frees a small
+ * device buffer.  TDP_EINVAL for a null fma_per_s, TDP_ECUDA on a CUDA error. */
+int tdp_fp64_fma_rate(double* fma_per_s, double* ms_out, void* stream);
 
 /* Per-kernel timing (a tracing aid): when enabled, every kernel the library
  * launches outside stream capture is bracketed by two CUDA events recorded

@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
     lib.tdp_solve_host.argtypes = [P, P, P, P, P, I64, I32, I32, I32, P]
     lib.tdp_status_code.argtypes = [ctypes.c_uint32]
     lib.tdp_last_status_bits.restype = ctypes.c_uint32
+    lib.tdp_fp64_fma_rate.argtypes = [P, P, P]
     return lib
 
 
@@ -87,12 +88,12 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
            "tdp_launch_count", "tdp_thomas_batched", "tdp_stage1", "tdp_profile_enable", "tdp_profile_summary",
            "tdp_solve_noalloc", "tdp_set_tuning", "tdp_get_tuning", "tdp_predict_s_batched", "tdp_predict_r",
            "tdp_load_rtable", "tdp_recursion_plan", "tdp_solve_const", "tdp_solve_multi", "tdp_solve_host",
-           "tdp_status_code", "tdp_last_status_bits")
+           "tdp_status_code", "tdp_last_status_bits", "tdp_fp64_fma_rate")
 
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP) = range(5)
 (TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S, TUNE_IFACE32, TUNE_REFINE_KEPT,
  TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B, TUNE_VTILE_L, TUNE_WINDOW, TUNE_WINDOW_HALO, TUNE_WAIT_LOG2,
- TUNE_WAIT_NEVER) = range(9, 24)
+ TUNE_WAIT_NEVER, TUNE_WINDOW_SW) = range(9, 25)
 RETIRED_TUNING_KEYS = (5, 6, 7, 8)
 
 
@@ -251,6 +252,15 @@ def tdp_launch_count() -> int:
 
 def tdp_profile_enable(on: bool):
     LIB.tdp_profile_enable(1 if on else 0)
+
+
+def tdp_fp64_fma_rate(stream=None):
+    """(binary64 FMAs per second, milliseconds of the timed launch) measured on
+    the current device by the library's diagnostic kernel."""
+    rate = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(LIB.tdp_fp64_fma_rate(ctypes.addressof(rate), ctypes.addressof(ms), _stream(stream)))
+    return rate.value, ms.value
 
 
 def tdp_profile_summary() -> dict:

@@ -263,10 +263,10 @@ void coop_build(Ctx& ctx, const double* ra, const double* rb, const double* rc, 
   P.ybase = (L > 0) ? ctx.ar->take<double>(Ml) : y;
 }
 
-// Grid of a cooperative launch: co-resident CTAs of `threads` threads, at
-// most `want`.
+// Grid of a cooperative launch: co-resident CTAs of `threads` threads (at
+// most max_per_sm per SM), at most `want`.
 template <typename K>
-int coop_grid(K kernel, int threads, int64_t want) {
+int coop_grid(K kernel, int threads, int64_t want, int max_per_sm = 1 << 30) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, int> per_sm_of;
   int dev = 0;
@@ -283,6 +283,7 @@ int coop_grid(K kernel, int threads, int64_t want) {
       per_sm = it->second;
     }
   }
+  per_sm = std::min(per_sm, max_per_sm);
   return int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(per_sm, 1)) * sm_count())));
 }
 
@@ -685,12 +686,12 @@ __global__ void k_check_offsets(const int64_t* __restrict__ off, int32_t batch, 
 // in one cooperative launch that runs only when a tile failed its checks.
 // off: a batch solved as one system (nsys systems), null for one system.
 // ---------------------------------------------------------------------------
-constexpr int kWinSW = 7;  // window rows per thread
 
 void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, const double* d, double* x,
                    int64_t n, int iters, const int64_t* off, int32_t nsys) {
   const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~1;
-  const int TR = kWinT * kWinSW - 2 * H;
+  const int SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
+  const int TR = kWinT * SW - 2 * H;
   const int64_t tiles = (n + TR - 1) / TR;
   unsigned* gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
   const int64_t m0 = (n + kExS - 1) / kExS;
@@ -710,12 +711,14 @@ void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, 
     post_launch(ctx, "offsets check");
   }
   WinParams W{a, b, c, d, x, n, H, TR, iters, off, nsys, gate, ctx.status};
-  auto wk = k_window_refine<kWinSW>;
+  auto wk = SW == 5 ? k_window_refine<5, 3> : k_window_refine<7, 2>;
   allow_smem(wk);
   pre_launch(ctx, "window_refine");
-  wk<<<unsigned(tiles), kWinT, WinSmem<kWinSW>::bytes(), ctx.stream>>>(W);
+  wk<<<unsigned(tiles), kWinT, SW == 5 ? WinSmem<5>::bytes() : WinSmem<7>::bytes(), ctx.stream>>>(W);
   post_launch(ctx, "windowed pass");
-  const int grid = coop_grid(k_exact_coop, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128);
+  // two CTAs per SM: the launch costs little when the gate is clear (every CTA
+  // returns at once), and the grid-stride loops cover any size when it is set
+  const int grid = coop_grid(k_exact_coop, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128, 2);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);

@@ -61,7 +61,7 @@ def solve(tdp, a, b, c, d, n, iters):
     return host(x), tdp.LIB.tdp_last_status_bits()
 
 
-TILE = 256 * 7 - 2 * 48  # owned rows per tile at the default halo
+TILE = 256 * 5 - 2 * 48  # owned rows per tile at the default geometry
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2])

@@ -101,12 +101,20 @@ class System:
         return System(*(v.astype(dtype) for v in (self.a, self.b, self.c, self.d, self.xstar)), self.offsets)
 
 
+def _ends(offsets: np.ndarray):
+    """First and last rows of the non-empty systems."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    keep = offsets[1:] > offsets[:-1]
+    return offsets[:-1][keep], offsets[1:][keep] - 1
+
+
 def matvec(a, b, c, x, offsets) -> np.ndarray:
     """d = A x for concatenated systems (couplings across systems dropped)."""
     a = a.copy()
     c = c.copy()
-    a[offsets[:-1]] = 0.0
-    c[offsets[1:] - 1] = 0.0
+    first, last = _ends(offsets)
+    a[first] = 0.0
+    c[last] = 0.0
     d = b * x
     d[1:] += a[1:] * x[:-1]
     d[:-1] += c[:-1] * x[1:]
@@ -118,8 +126,9 @@ def _values(seed: int, offsets: np.ndarray) -> System:
     a = uniform(seed, STREAM_A, n, -1.0, 1.0)
     b = uniform(seed, STREAM_B, n, 4.0, 8.0)
     c = uniform(seed, STREAM_C, n, -1.0, 1.0)
-    a[offsets[:-1]] = 0.0
-    c[offsets[1:] - 1] = 0.0
+    first, last = _ends(offsets)
+    a[first] = 0.0
+    c[last] = 0.0
     x = uniform(seed, STREAM_X, n, -1.0, 1.0)
     d = matvec(a, b, c, x, offsets)
     return System(a, b, c, d, x, offsets.astype(np.int64))
