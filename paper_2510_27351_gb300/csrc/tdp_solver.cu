@@ -710,7 +710,7 @@ void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, 
     k_check_offsets<<<grid_for(int64_t(nsys) + 1, 256), 256, 0, ctx.stream>>>(off, nsys, n, ctx.status);
     post_launch(ctx, "offsets check");
   }
-  WinParams W{a, b, c, d, x, n, H, TR, iters, off, nsys, gate, ctx.status};
+  WinParams W{a, b, c, d, x, n, H, TR, iters, off, nsys, gate, ctx.status, 1ll << ctx.wait_log2};
   auto wk = SW == 5 ? k_window_refine<5, 3> : k_window_refine<7, 2>;
   allow_smem(wk);
   pre_launch(ctx, "window_refine");
