@@ -43,10 +43,27 @@ extern "C" {
 /* Precision of a solve.
  *  TDP_F64        binary64 storage, binary64 arithmetic.
  *  TDP_F32        binary32 storage, binary32 arithmetic for the sub-system
- *                 eliminations and substitutions, binary64 interface solve.
+ *                 eliminations and substitutions, binary64 interface solve;
+ *                 by default single systems and batches take the windowed
+ *                 single pass (TDP_TUNE_WINDOW32, below).
  *  TDP_F32_REFINE binary64 storage; binary32 eliminations/substitutions with a
  *                 binary64 residual r = d - A x and correction x += delta
- *                 (iterative refinement), binary64 interface solve. */
+ *                 (iterative refinement), binary64 interface solve; by
+ *                 default single systems and batches take the windowed
+ *                 single pass (TDP_TUNE_WINDOW, below).
+ *
+ * The windowed single pass (not in the paper: for binary32 arithmetic, where
+ * GB300's binary64 pipe does not bound the solve) reads the inputs once:
+ * every tile of about 1200 rows is solved inside a window with 48 halo rows
+ * on each side (binary32 partition solve of the window, its interface system
+ * included, then for TDP_F32_REFINE the binary64 residual and corrections
+ * on chip).  Each tile checks at run time that its window rows are
+ * diagonally dominant and that the decay of A^-1 across each halo bounds the
+ * windowed solution's distance from x (by 2^-45 ||x|| for TDP_F32_REFINE,
+ * 2^-30 ||x|| for TDP_F32); if any tile fails, the exact partition method
+ * solves the whole system in binary64 in one further cooperative launch,
+ * and the status word gets its informational fallback bit (8).  The size s
+ * does not apply to the windowed pass. */
 typedef enum { TDP_F64 = 0, TDP_F32 = 1, TDP_F32_REFINE = 2 } tdp_dtype;
 
 #define TDP_OK 0
@@ -112,11 +129,12 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
 /* tdp_solve with HOST arrays (a, b, c, d in, x out; n elements each), for
  * callers whose data are not on the device yet.  Pinned host memory
  * (cudaHostAlloc / cudaHostRegister) lets the copies overlap the solve: the
- * binary64 and binary32 solves run in about eight chunks, Stage 1 of a chunk
- * while the next one is copied in, Stage 3 of a chunk while the previous one is
- * copied out (a second stream that the call creates and releases); the answer
- * is the one tdp_solve gives, bit for bit.  The refinement copies everything
- * in, solves and copies out.  Asynchronous on `stream` like tdp_solve: x is
+ * binary64 solve (and the binary32 one with TDP_TUNE_WINDOW32 = 0) runs in
+ * about eight chunks, Stage 1 of a chunk while the next one is copied in,
+ * Stage 3 of a chunk while the previous one is copied out (a second stream
+ * that the call creates and releases); the answer is the one tdp_solve
+ * gives, bit for bit.  The windowed passes (refinement and, by default,
+ * binary32) copy everything in, solve and copy out.  Asynchronous on `stream` like tdp_solve: x is
  * complete when the stream's work is.  The device copies of the arrays live
  * in the workspace (5n elements).  Other arguments and errors as tdp_solve;
  * x must not overlap an input. */
@@ -279,14 +297,17 @@ int64_t tdp_launch_count(void);
                                    interleaved tile (a quarter less shared memory per row) */
 #define TDP_TUNE_VTILE_L 19     /* 1: binary32 storage runs Stage 1 and Stage 3 on padded block-major tiles
                                    (each block's rows contiguous in shared memory) */
-#define TDP_TUNE_WINDOW 20      /* 1: TDP_F32_REFINE single systems and batches solved as one system take the
-                                   windowed single pass (see tdp_solve) */
-#define TDP_TUNE_WINDOW_HALO 21 /* halo rows on each side of a tile of the windowed pass [16, 64], even */
+#define TDP_TUNE_WINDOW 20      /* 1: TDP_F32_REFINE single systems and batches take the windowed single pass
+                                   (see tdp_solve) */
+#define TDP_TUNE_WINDOW_HALO 21 /* halo rows on each side of a tile of the windowed pass [16, 64], rounded down
+                                   to a multiple of 4 */
 #define TDP_TUNE_WAIT_LOG2 22   /* every bounded device wait gives up after 2^value clock cycles [10, 40] */
 #define TDP_TUNE_WAIT_NEVER 23  /* 1 (testing only): grid barriers wait for one arrival more than the grid has,
                                    so every such wait runs out and the call reports TDP_ETIMEOUT */
 #define TDP_TUNE_WINDOW_SW 24   /* rows per thread in the windowed pass's window: 5 or 7 (odd, so that the
                                    threads' strided shared-memory reads avoid bank conflicts) */
+#define TDP_TUNE_WINDOW32 25    /* 1: TDP_F32 single systems and batches take the windowed single pass too
+                                   (binary32 solve of each window, no refinement; exact fallback) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

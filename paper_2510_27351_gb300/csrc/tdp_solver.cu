@@ -687,15 +687,17 @@ __global__ void k_check_offsets(const int64_t* __restrict__ off, int32_t batch, 
 // off: a batch solved as one system (nsys systems), null for one system.
 // ---------------------------------------------------------------------------
 
-void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, const double* d, double* x,
-                   int64_t n, int iters, const int64_t* off, int32_t nsys) {
-  const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~1;
+template <typename S>
+void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
+                 const int64_t* off, int32_t nsys) {
+  constexpr bool REFINE = sizeof(S) == 8;
+  const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~3;
   const int SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
   const int TR = kWinT * SW - 2 * H;
   const int64_t tiles = (n + TR - 1) / TR;
   unsigned* gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
   const int64_t m0 = (n + kExS - 1) / kExS;
-  ExactParams E{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
+  ExactParams<S> E{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
   E.ra = ctx.ar->take<double>(2 * m0);
   E.rb = ctx.ar->take<double>(2 * m0);
   E.rc = ctx.ar->take<double>(2 * m0);
@@ -710,15 +712,21 @@ void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, 
     k_check_offsets<<<grid_for(int64_t(nsys) + 1, 256), 256, 0, ctx.stream>>>(off, nsys, n, ctx.status);
     post_launch(ctx, "offsets check");
   }
-  WinParams W{a, b, c, d, x, n, H, TR, iters, off, nsys, gate, ctx.status, 1ll << ctx.wait_log2};
-  auto wk = SW == 5 ? k_window_refine<5, 3> : k_window_refine<7, 2>;
+  // binary64 storage: the windowed solution within 2^-45 ||x|| (the refinement
+  // goes below binary32 rounding); binary32 storage: within 2^-30 ||x||
+  const float tau = REFINE ? kWinTau : 1.0f / 2147483648.0f;
+  WinParams<S> W{a, b, c, d, x, n, H, TR, REFINE ? iters : 0, tau, off, nsys, gate, ctx.status,
+                 1ll << ctx.wait_log2};
+  auto wk = SW == 5 ? k_window<S, 5, REFINE ? 3 : 4> : k_window<S, 7, 2>;
   allow_smem(wk);
-  pre_launch(ctx, "window_refine");
-  wk<<<unsigned(tiles), kWinT, SW == 5 ? WinSmem<5>::bytes() : WinSmem<7>::bytes(), ctx.stream>>>(W);
+  const char* name = REFINE ? "window_refine" : "window_f32";
+  pre_launch(ctx, name);
+  wk<<<unsigned(tiles), kWinT, SW == 5 ? WinSmem<S, 5>::bytes() : WinSmem<S, 7>::bytes(), ctx.stream>>>(W);
   post_launch(ctx, "windowed pass");
   // two CTAs per SM: the launch costs little when the gate is clear (every CTA
   // returns at once), and the grid-stride loops cover any size when it is set
-  const int grid = coop_grid(k_exact_coop, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128, 2);
+  auto ek = k_exact_coop<S>;
+  const int grid = coop_grid(ek, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128, 2);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);
@@ -730,8 +738,7 @@ void window_refine(Ctx& ctx, const double* a, const double* b, const double* c, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   pre_launch(ctx, "exact_fallback");
-  ctx.fail(cudaLaunchKernelEx(&cfg, k_exact_coop, E, P, (const unsigned*)gate, gate + 1, ctx.status),
-           "exact fallback launch");
+  ctx.fail(cudaLaunchKernelEx(&cfg, ek, E, P, (const unsigned*)gate, gate + 1, ctx.status), "exact fallback launch");
   post_launch(ctx, "exact fallback");
 }
 
@@ -1118,8 +1125,13 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
   ctx.rec_batch = 1;
   ctx.rec_dt = dt;
   if (dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0) {
-    window_refine(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, n,
-                  refine_iters, nullptr, 0);
+    window_pass<double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, n,
+                        refine_iters, nullptr, 0);
+    return;
+  }
+  if (dt == TDP_F32 && ctx.window32 && ctx.rec_mode == 0) {
+    window_pass<float>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)d, (float*)x, n, 0,
+                       nullptr, 0);
     return;
   }
   if (s > n) s = int(std::max<int64_t>(2, n));
@@ -1233,7 +1245,9 @@ void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const voi
   char* xd = ctx.ar->take<char>(size_t(n) * el);
   const char* hsrc[4] = {(const char*)a, (const char*)b, (const char*)c, (const char*)d};
   char* dsrc[4] = {ad, bd, cd, dd};
-  const bool chunked = ctx.vtile && (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0));
+  // (binary32 storage takes the windowed pass, whose single read leaves no
+  // Stage 1 / Stage 3 split to pipeline the copies against)
+  const bool chunked = ctx.vtile && (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0 && !ctx.window32));
   if (!chunked) {
     if (!ctx.dry && ctx.err == cudaSuccess)
       for (int i = 0; i < 4; ++i)
@@ -1341,8 +1355,13 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
   if (batch <= 0 || total_n <= 0) return;
   if (dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0 && !ctx.per_system_s) {
     // every batch as one system: the windowed pass cuts the couplings between systems
-    window_refine(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, total_n,
-                  refine_iters, offsets, batch);
+    window_pass<double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x,
+                        total_n, refine_iters, offsets, batch);
+    return;
+  }
+  if (dt == TDP_F32 && ctx.window32 && ctx.rec_mode == 0 && !ctx.per_system_s) {
+    window_pass<float>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)d, (float*)x, total_n, 0,
+                       offsets, batch);
     return;
   }
   const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;

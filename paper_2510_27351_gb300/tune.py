@@ -311,8 +311,15 @@ def autotune_batched(offsets, a, b, c, d, x, dtype, refine_iters=0, s_grid=(8, 1
 # ---------------------------------------------------------------------------
 # the sweep (GPU)
 # ---------------------------------------------------------------------------
-def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(1,), reps=5, s_grid=S_GRID,
+def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(1,), trials=5, s_grid=S_GRID,
           max_rows=1 << 28):
+    """Time every s of the grid for every size, batch and precision: one solve
+    captured into a CUDA graph and replayed (device time only, no host launch
+    gaps, which dominate at small sizes), the fastest of ``trials`` timed
+    trials of about 20 ms each (launch noise only ever adds time).  The
+    binary32 + refinement rows time the exact three-pass schedule, the one
+    that uses s, and so do the binary32 rows (the windowed passes have a
+    fixed geometry)."""
     import torch
 
     import paper_2510_27351_gb300 as tdp
@@ -324,41 +331,70 @@ def sweep(out, dtypes=(0, 1, 2), log2_lo=10.0, log2_hi=28.0, step=0.5, batches=(
     dev = torch.device("cuda")
     g = torch.Generator(device=dev)
     g.manual_seed(0)
+    stream = torch.cuda.Stream()  # one stream: the library keeps one workspace per stream
     sizes = []
     x = log2_lo
     while x <= log2_hi + 1e-9:
         sizes.append(int(round(2 ** x)))
         x += step
-    with open(out, "a") as fh:
-        for batch in batches:
-            for n in sizes:
-                total = n * batch
-                if total > max_rows:
-                    continue
-                for dt in dtypes:
-                    todo = [s for s in s_grid if (dt, n, batch, s) not in done and s <= max(4, n)]
-                    if not todo:
+    keys = (tdp.TUNE_WINDOW, tdp.TUNE_WINDOW32)  # the windowed passes ignore s: time the exact schedules
+    old_window = [tdp.tdp_get_tuning(k) for k in keys]
+    for k in keys:
+        tdp.tdp_set_tuning(k, 0)
+    try:
+        with open(out, "a") as fh:
+            for batch in batches:
+                for n in sizes:
+                    total = n * batch
+                    if total > max_rows:
                         continue
-                    st = torch.float32 if dt == 1 else torch.float64
-                    a = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
-                    b = (torch.rand(total, generator=g, device=dev, dtype=st) * 4 + 4)
-                    c = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
-                    d = (torch.rand(total, generator=g, device=dev, dtype=st) * 2 - 1)
-                    xo = torch.empty_like(d)
-                    off = torch.arange(batch + 1, device=dev, dtype=torch.int64) * n
-                    it = 1 if dt == 2 else 0
-                    for s in todo:
-                        if batch == 1:
-                            fn = lambda: tdp.tdp_solve(a, b, c, d, xo, total, s, dt, it)
-                        else:
-                            fn = lambda: tdp.tdp_solve_batched(off, batch, total, a, b, c, d, xo, s, dt, it)
-                        r = reps if total >= (1 << 20) else 4 * reps
-                        # the best of three timed trials: launch noise only ever adds time
-                        ms = min(_time_ms(fn, r) for _ in range(3))
-                        fh.write(json.dumps({"dtype": dt, "n": n, "batch": batch, "s": s, "ms": ms}) + "\n")
-                        fh.flush()
-                    del a, b, c, d, xo
-                    torch.cuda.empty_cache()
+                    for dt in dtypes:
+                        todo = [s for s in s_grid if (dt, n, batch, s) not in done and s <= max(4, n)]
+                        if not todo:
+                            continue
+                        a, b, c, d = _random_system(total, dt, g, dev)
+                        xo = torch.empty_like(d)
+                        off = torch.arange(batch + 1, device=dev, dtype=torch.int64) * n
+                        it = 1 if dt == 2 else 0
+                        for s in todo:
+                            if batch == 1:
+                                fn = lambda st: tdp.tdp_solve(a, b, c, d, xo, total, s, dt, it, st)
+                            else:
+                                fn = lambda st: tdp.tdp_solve_batched(off, batch, total, a, b, c, d, xo, s, dt, it,
+                                                                      st)
+                            ms = _graph_time_ms(tdp, fn, stream, trials)
+                            fh.write(json.dumps({"dtype": dt, "n": n, "batch": batch, "s": s, "ms": ms}) + "\n")
+                            fh.flush()
+                        del a, b, c, d, xo
+                        torch.cuda.empty_cache()
+    finally:
+        for k, v in zip(keys, old_window):
+            tdp.tdp_set_tuning(k, v)
+
+
+def _graph_time_ms(tdp, fn, stream, trials):
+    """Milliseconds per solve: fn(stream) captured into a CUDA graph, replayed
+    back to back; the fastest of ``trials`` trials of about 20 ms."""
+    import torch
+
+    graph = tdp.CapturedSolve(fn, stream)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        stream.synchronize()
+        reps = int(max(3, min(500, 20.0 / max(1e-3, e0.elapsed_time(e1)))))
+        best = float("inf")
+        for _ in range(trials):
+            e0.record(stream)
+            for _ in range(reps):
+                graph.replay()
+            e1.record(stream)
+            stream.synchronize()
+            best = min(best, e0.elapsed_time(e1) / reps)
+    del graph
+    return best
 
 
 def autotune_const(fn, s_grid=(8, 16, 32, 64, 128), reps=10):
@@ -544,7 +580,7 @@ def main(argv=None):
     p.add_argument("--hi", type=float, default=28.0)
     p.add_argument("--step", type=float, default=0.5)
     p.add_argument("--batches", default="1")
-    p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--trials", type=int, default=5)
     p = sub.add_parser("table")
     p.add_argument("--sweep", required=True)
     p.add_argument("--out")
@@ -569,7 +605,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.cmd == "sweep":
         sweep(args.out, tuple(int(v) for v in args.dtypes.split(",")), args.lo, args.hi, args.step,
-              tuple(int(v) for v in args.batches.split(",")), args.reps)
+              tuple(int(v) for v in args.batches.split(",")), args.trials)
     elif args.cmd == "table":
         write_table(build_table(load_sweep(args.sweep)), args.out, args.inc)
     elif args.cmd == "evaluate":

@@ -78,6 +78,28 @@ def test_single_vs_oracle(tdp, n, code):
         assert e <= TOL[code], (n, s, code, e)
 
 
+@pytest.mark.parametrize("code", [1, 2])
+def test_exact_schedules_vs_oracle(tdp, code):
+    """The exact binary32 and binary32 + refinement schedules (the windowed
+    passes off: Stage 1, the binary64 interface recursion, Stage 3; the
+    three-pass refinement) against the oracle, every size and sub-system size
+    of test_single_vs_oracle."""
+    keys = (tdp.TUNE_WINDOW, tdp.TUNE_WINDOW32)
+    old = [tdp.tdp_get_tuning(k) for k in keys]
+    for k in keys:
+        tdp.tdp_set_tuning(k, 0)
+    try:
+        for n in SIZES:
+            S = W.single(n, seed=n + 1)
+            ref = oracle.thomas(S.a, S.b, S.c, S.d)
+            for s in SUBS:
+                e = oracle.rel_err(_solve(tdp, S, s, code), ref)
+                assert e <= TOL[code], (n, s, e)
+    finally:
+        for k, v in zip(keys, old):
+            tdp.tdp_set_tuning(k, v)
+
+
 def test_fp32_really_single_precision(tdp):
     S = W.single(50_000, seed=3)
     ref = oracle.thomas(S.a, S.b, S.c, S.d)
@@ -550,6 +572,8 @@ def test_padded_binary32_tiles_match_interleaved_tiles(tdp):
     import torch
 
     old = tdp.tdp_get_tuning(tdp.TUNE_VTILE_L)
+    old_w = tdp.tdp_get_tuning(tdp.TUNE_WINDOW32)
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW32, 0)  # the tiles belong to the exact binary32 path
     cases = [W.single(n, seed=n) for n in (1, 2, 3, 5, 7, 1000, 4096, 4099, 100_003, 1 << 20, (1 << 22) + 37)]
     Sb = W.batched(sizes=[5000, 1, 0, 8193, 4096, 12000, 2, 7, 9999, 3, 6500], seed=11)
     try:
@@ -574,6 +598,7 @@ def test_padded_binary32_tiles_match_interleaved_tiles(tdp):
                 assert oracle.rel_err(got[1], ref) <= TOL[1], (S.n, s)
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, old)
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW32, old_w)
 
 
 @pytest.mark.parametrize("code", [0, 1])
@@ -704,17 +729,23 @@ def test_device_wait_timeout_reported(tdp):
     n, s = 1 << 20, 16  # interface system of 131,072 rows: one cooperative launch
     S = W.single(n, seed=31)
     ref = oracle.thomas(S.a, S.b, S.c, S.d)
-    old = (tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER), tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2))
+    old = (tdp.tdp_get_tuning(tdp.TUNE_WAIT_NEVER), tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2),
+           tdp.tdp_get_tuning(tdp.TUNE_WINDOW32))
     tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, 14)
     tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, 1)
+    # the windowed passes wait on no grid barrier unless they fall back
+    # (tests/test_gpu_window.py makes that fallback's wait run out): binary32
+    # here takes the exact schedule
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW32, 0)
     try:
-        for code in (0, 1, 2):
+        for code in (0, 1):
             with pytest.raises(tdp.TdpError) as ei:
                 _solve(tdp, S, s, code)
             assert ei.value.code == tdp.ETIMEOUT, code
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
         tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW32, old[2])
     for code in (0, 2):
         assert oracle.rel_err(_solve(tdp, S, s, code), ref) <= TOL[code]
     # unchecked mode: the call returns at once and tdp_status reports the timeout later

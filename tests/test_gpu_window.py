@@ -202,3 +202,40 @@ def test_window_fallback_timeout_reported(tdp):
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_WAIT_NEVER, old[0])
         tdp.tdp_set_tuning(tdp.TUNE_WAIT_LOG2, old[1])
+
+
+def solve32(tdp, a, b, c, d, n, offsets=None):
+    import torch
+
+    A, B, C, D = (dev(np.asarray(v, dtype=np.float32)) for v in (a, b, c, d))
+    x = torch.full_like(D, float("nan"))
+    if offsets is None:
+        tdp.tdp_solve(A, B, C, D, x, n, 0, tdp.F32, 0)
+    else:
+        tdp.tdp_solve_batched(dev(offsets), len(offsets) - 1, n, A, B, C, D, x, 0, tdp.F32, 0)
+    torch.cuda.synchronize()
+    return host(x), tdp.LIB.tdp_last_status_bits()
+
+
+def test_window_binary32_storage(tdp):
+    """Binary32 storage through the windowed pass (no refinement; the
+    window's bound is 2^-30 ||x||): tile-boundary sizes, a batch with tiny and
+    empty systems, and inputs that fail the bound (fallback: the exact
+    binary64 solve, rounded to binary32).  Tolerance 1e-5 against the
+    oracle's binary64 Thomas of the binary32-rounded inputs."""
+    for n in (1, 2, 3, 5, 97, TILE - 1, TILE, TILE + 1, 2 * TILE + 3, 100_003, (1 << 20) + 1):
+        S = W.single(n, seed=n + 29)
+        a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (S.a, S.b, S.c, S.d))
+        x, bits = solve32(tdp, a, b, c, d, n)
+        assert not bits & tdp.ST_FALLBACK, n
+        assert oracle.rel_err(x, oracle.thomas(a, b, c, d)) <= 1e-5, n
+    Sb = W.batched(sizes=[0, 1, 2, 3, 0, 5, 64, 1, 1700, 47, 48, 0, 5000, 300], seed=8)
+    a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+    x, bits = solve32(tdp, a, b, c, d, Sb.n, Sb.offsets)
+    assert not bits & tdp.ST_FALLBACK
+    assert per_system_err(x, oracle.thomas_batched(a, b, c, d, offsets=Sb.offsets), Sb.offsets) <= 1e-5
+    Sw = W.weak(200_003, 1e-3, seed=9)
+    a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (Sw.a, Sw.b, Sw.c, Sw.d))
+    x, bits = solve32(tdp, a, b, c, d, Sw.n)
+    assert bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, oracle.thomas(a, b, c, d)) <= 1e-5
