@@ -268,16 +268,70 @@ def evaluate_transfer(rows):
 _AUTOTUNE_CACHE = {}
 
 
+def _timed_ms(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune_window(offsets, a, b, c, d, x, dtype, refine_iters=0, sw_grid=(5, 7), halos=(32, 48, 64), reps=3):
+    """Pick the windowed pass's block shape (rows per thread, halo rows) for
+    ``tdp_solve_batched`` on this batch by timing every pair (a halo too short
+    for the batch's decay shows up as the time of the exact fallback), set
+    the knobs TDP_TUNE_WINDOW_SW and TDP_TUNE_WINDOW_HALO and return
+    (rows per thread, halo, ms).  Cached per (dtype, total rows, batch)."""
+    import paper_2510_27351_gb300 as tdp
+
+    batch, total = offsets.numel() - 1, d.numel()
+    key = ("window", int(dtype), int(total), int(batch), int(refine_iters))
+    if key not in _AUTOTUNE_CACHE:
+        old = (tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW), tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO))
+        best = None
+        try:
+            for sw in sw_grid:
+                for h in halos:
+                    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, sw)
+                    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, h)
+                    ms = _timed_ms(lambda: tdp.tdp_solve_batched(offsets, batch, total, a, b, c, d, x, 0, dtype,
+                                                                 refine_iters), reps)
+                    if best is None or ms < best[2]:
+                        best = (sw, h, ms)
+        finally:
+            tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, old[0])
+            tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, old[1])
+        _AUTOTUNE_CACHE[key] = best
+    sw, h, ms = _AUTOTUNE_CACHE[key]
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, sw)
+    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, h)
+    return sw, h, ms
+
+
 def autotune_batched(offsets, a, b, c, d, x, dtype, refine_iters=0, s_grid=(8, 12, 16, 24, 32, 48),
                      budgets=(32 * 1024, 64 * 1024, 100 * 1024), reps=3):
     """Pick (s, shared-memory budget per CTA) for ``tdp_solve_batched`` on
     this batch by timing every pair, set the budget knob and return
-    (s, budget, ms).  Results are cached per (dtype, total rows, batch)."""
+    (s, budget, ms).  Results are cached per (dtype, total rows, batch).
+    A precision whose batches take the windowed pass (binary32 + refinement,
+    binary32; s does not apply there) gets its block shape tuned instead
+    (autotune_window) and (0, the current budget, ms) back."""
     import torch
 
     import paper_2510_27351_gb300 as tdp
 
     batch, total = offsets.numel() - 1, d.numel()
+    windowed = ((int(dtype) == tdp.F32_REFINE and tdp.tdp_get_tuning(tdp.TUNE_WINDOW))
+                or (int(dtype) == tdp.F32 and tdp.tdp_get_tuning(tdp.TUNE_WINDOW32)))
+    if windowed:
+        _, _, ms = autotune_window(offsets, a, b, c, d, x, dtype, refine_iters, reps=reps)
+        return 0, tdp.tdp_get_tuning(tdp.TUNE_SMEM_BUDGET), ms
     key = (int(dtype), int(total), int(batch), int(refine_iters))
     if key in _AUTOTUNE_CACHE:
         s, budget, ms = _AUTOTUNE_CACHE[key]

@@ -333,9 +333,22 @@ def test_cuda_graph_capture_and_autotune(tdp):
     off = dev(Sb.offsets)
     x = torch.empty_like(d)
     tdp.tdp_set_checked(False)
+    shape = (tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW), tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO),
+             tdp.tdp_get_tuning(tdp.TUNE_SMEM_BUDGET))
     try:
+        # the refinement's batches take the windowed pass: its block shape is tuned
         s, budget, ms = tune.autotune_batched(off, a, b, c, d, x, 2, 1, s_grid=(8, 16), budgets=(32768, 65536))
-        assert s in (8, 16) and budget in (32768, 65536) and ms > 0
+        assert s == 0 and ms > 0
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW) in (5, 7)
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO) in (32, 48, 64)
+        # the exact schedule's (s, shared-memory budget)
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 0)
+        try:
+            s2, budget, ms2 = tune.autotune_batched(off, a, b, c, d, x, 2, 1, s_grid=(8, 16),
+                                                    budgets=(32768, 65536))
+        finally:
+            tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 1)
+        assert s2 in (8, 16) and budget in (32768, 65536) and ms2 > 0
         graph = tdp.CapturedSolve(lambda st: tdp.tdp_solve_batched(off, Sb.batch, Sb.n, a, b, c, d, x, s, 2, 1, st))
         for seed in (1, 2):  # new right-hand sides in the captured buffers
             d2 = W.matvec(Sb.a, Sb.b, Sb.c, W.uniform(seed, 9, Sb.n, -1, 1), Sb.offsets)
@@ -348,6 +361,9 @@ def test_cuda_graph_capture_and_autotune(tdp):
         tdp.tdp_status()
     finally:
         tdp.tdp_set_checked(True)
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, shape[0])
+        tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, shape[1])
+        tdp.tdp_set_tuning(tdp.TUNE_SMEM_BUDGET, shape[2])
 
 
 @pytest.mark.parametrize("code", [0, 1, 2])
