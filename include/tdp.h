@@ -308,6 +308,8 @@ int64_t tdp_launch_count(void);
                                    threads' strided shared-memory reads avoid bank conflicts) */
 #define TDP_TUNE_WINDOW32 25    /* 1: TDP_F32 single systems and batches take the windowed single pass too
                                    (binary32 solve of each window, no refinement; exact fallback) */
+#define TDP_TUNE_WINDOW_PREFETCH 26 /* the CTA of tile t of the windowed pass asks L2 for the window of tile
+                                   t + value before loading its own [0, 4096], default 128; 0 = no prefetch */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

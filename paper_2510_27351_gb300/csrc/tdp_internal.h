@@ -70,6 +70,7 @@ struct Ctx {
   bool vtile_l = true;         // binary32 storage: padded block-major tiles (TDP_VTILE_L=0 off)
   bool window = true;          // windowed single pass for binary32 + binary64 refinement (TDP_WINDOW=0 off)
   bool window32 = true;        // windowed single pass for binary32 storage (TDP_WINDOW32=0 off)
+  int window_prefetch = 128;   // L2 prefetch distance of the windowed pass in tiles (TDP_WINDOW_PREFETCH)
   int window_halo = 48;        // its halo rows on each side of a tile (TDP_WINDOW_HALO)
   int window_sw = 5;           // its window rows per thread, 5 or 7 (TDP_WINDOW_SW)
   int wait_log2 = 31;          // bounded device waits give up after 2^wait_log2 cycles (TDP_WAIT_LOG2)

@@ -716,7 +716,7 @@ void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x,
   // goes below binary32 rounding); binary32 storage: within 2^-30 ||x||
   const float tau = REFINE ? kWinTau : 1.0f / 2147483648.0f;
   WinParams<S> W{a, b, c, d, x, n, H, TR, REFINE ? iters : 0, tau, off, nsys, gate, ctx.status,
-                 1ll << ctx.wait_log2};
+                 1ll << ctx.wait_log2, ctx.window_prefetch};
   auto wk = SW == 5 ? k_window<S, 5, REFINE ? 3 : 4> : k_window<S, 7, 2>;
   allow_smem(wk);
   const char* name = REFINE ? "window_refine" : "window_f32";
