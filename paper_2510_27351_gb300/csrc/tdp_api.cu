@@ -85,13 +85,14 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // TDP_VTILE_L (1: binary32 storage runs Stage 1 and Stage 3 on padded
 // block-major tiles), TDP_WINDOW (1: the windowed single pass for binary32
 // solves with binary64 refinement), TDP_WINDOW_HALO (its halo rows per side),
-// TDP_WAIT_LOG2 (log2 of the clock-cycle budget of every bounded device wait)
-// and TDP_WAIT_NEVER (1: the grid barriers wait for one arrival more than
-// the grid has, so that every such wait runs out; for testing the timeout
-// path), TDP_WINDOW_SW (rows per thread of the windowed pass's window, 5
-// or 7), TDP_WINDOW32 (1: binary32 storage takes the windowed pass too) and
-// TDP_WINDOW_PREFETCH (the windowed pass's L2 prefetch distance in tiles).  Keys 5 to 8 belonged to variants that were measured slower and
-// removed; they are rejected.
+// TDP_WAIT_LOG2 (log2 of the clock-cycle budget of every bounded device wait),
+// TDP_WAIT_NEVER (1: the grid barriers wait for one arrival more than the
+// grid has, so that every such wait runs out; for testing the timeout path),
+// TDP_WINDOW_SW (rows per thread of the windowed pass's window, 5 or 7),
+// TDP_WINDOW32 (1: binary32 storage takes the windowed pass too) and
+// TDP_WINDOW_PREFETCH (the windowed pass's L2 prefetch distance in tiles).
+// Keys 5 to 8 belonged to variants that were measured slower and removed;
+// they are rejected.
 struct Knob {
   const char* env;
   int lo, hi;

@@ -128,7 +128,8 @@ def test_tuning_knobs_validate_and_round_trip():
         # every key the header declares answers with its default range
         defaults = {tdp.TUNE_IFACE32: 0, tdp.TUNE_REFINE_KEPT: 1, tdp.TUNE_SEGMENTED: 1, tdp.TUNE_REFINE3: 1,
                     tdp.TUNE_PER_SYSTEM_S: 0, tdp.TUNE_VTILE: 1, tdp.TUNE_COOP: 1, tdp.TUNE_COOP_REG: 1,
-                    tdp.TUNE_BATCH_FLAT: 1, tdp.TUNE_VTILE_B: 1, tdp.TUNE_VTILE_L: 1, tdp.TUNE_WINDOW: 1, tdp.TUNE_WINDOW32: 1,
+                    tdp.TUNE_BATCH_FLAT: 1, tdp.TUNE_VTILE_B: 1, tdp.TUNE_VTILE_L: 1, tdp.TUNE_WINDOW: 1,
+                    tdp.TUNE_WINDOW32: 1,
                     tdp.TUNE_WAIT_NEVER: 0}
         for key, v in defaults.items():
             assert tdp.tdp_get_tuning(key) in (0, 1) and tdp.tdp_get_tuning(key) == v, key
