@@ -309,11 +309,13 @@ def thomas_batched(offsets, a, b, c, d, out=None, stream=None):
     return x
 
 
-def solve_backward(offsets, a, b, c, x, g, s: int = 0, stream=None):
-    """(grad_a, grad_b, grad_c, grad_d) of L given x = A^{-1} d and g = dL/dx."""
+def solve_backward(offsets, a, b, c, x, g, s: int = 0, refine: bool = False, stream=None):
+    """(grad_a, grad_b, grad_c, grad_d) of L given x = A^{-1} d and g = dL/dx;
+    ``refine`` (float64 tensors): the transposed solve in binary32 with one
+    binary64 correction."""
     ga, gb, gc, gd = (torch.empty_like(x) for _ in range(4))
     tdp_solve_backward(offsets, offsets.numel() - 1, x.numel(), a, b, c, x, g, ga, gb, gc, gd, s,
-                       _dtype_code(x, False), stream)
+                       _dtype_code(x, refine), stream)
     return ga, gb, gc, gd
 
 
@@ -350,21 +352,24 @@ class TridiagonalSolve(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, offsets, a, b, c, d, s=0):
-        x = solve_batched(offsets, a, b, c, d, s=s)
+    def forward(ctx, offsets, a, b, c, d, s=0, refine=False):
+        x = solve_batched(offsets, a, b, c, d, s=s, refine=refine)
         ctx.save_for_backward(offsets, a, b, c, x)
         ctx.s = s
+        ctx.refine = refine
         return x
 
     @staticmethod
     def backward(ctx, g):
         offsets, a, b, c, x = ctx.saved_tensors
-        ga, gb, gc, gd = solve_backward(offsets, a, b, c, x, g.contiguous(), s=ctx.s)
-        return None, ga, gb, gc, gd, None
+        ga, gb, gc, gd = solve_backward(offsets, a, b, c, x, g.contiguous(), s=ctx.s, refine=ctx.refine)
+        return None, ga, gb, gc, gd, None, None
 
 
-def tridiagonal_solve(a, b, c, d, offsets=None, s: int = 0):
-    """Differentiable solve; ``offsets`` defaults to one system."""
+def tridiagonal_solve(a, b, c, d, offsets=None, s: int = 0, refine: bool = False):
+    """Differentiable solve; ``offsets`` defaults to one system; ``refine``
+    (float64 tensors): forward and adjoint solves in binary32 with one
+    binary64 correction."""
     if offsets is None:
         offsets = torch.tensor([0, d.numel()], dtype=torch.int64, device=d.device)
-    return TridiagonalSolve.apply(offsets, a, b, c, d, s)
+    return TridiagonalSolve.apply(offsets, a, b, c, d, s, refine)

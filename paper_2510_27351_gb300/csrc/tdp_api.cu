@@ -625,7 +625,7 @@ int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, c
                        const void* c, const void* x, const void* g, void* grad_a, void* grad_b, void* grad_c,
                        void* grad_d, int32_t s, tdp_dtype dtype, void* stream) {
   if (batch < 1) return set_error(TDP_EINVAL, "tdp_solve_backward: batch must be >= 1");
-  int rc = check_common(total_n < 1 ? 1 : total_n, s, dtype, 0, "tdp_solve_backward", false);
+  int rc = check_common(total_n < 1 ? 1 : total_n, s, dtype, 0, "tdp_solve_backward");
   if (rc) return rc;
   if (!offsets) return set_error(TDP_EINVAL, "tdp_solve_backward: null offsets");
   if (total_n == 0) return TDP_OK;

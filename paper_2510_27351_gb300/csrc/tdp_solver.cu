@@ -1478,7 +1478,8 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
   // The transposed diagonals carry explicit zeros at every system boundary,
   // so the batch is one block-diagonal tridiagonal system of total_n rows:
   // it takes the single-system path (no block map; 16-byte tiles).
-  solve_single(ctx, aT, b, cT, g, lam, total_n, s, dt, 0);
+  // (binary32 + refinement: one binary64 correction)
+  solve_single(ctx, aT, b, cT, g, lam, total_n, s, dt, dt == TDP_F32_REFINE ? 1 : 0);
   if (!ctx.dry && ctx.err == cudaSuccess && (ga || gb || gc)) {
     pre_launch(ctx, "gradients");
     if (el == 8)

@@ -58,8 +58,9 @@ def test_bad_arguments_rejected_on_host():
     assert "aligned" in tdp.tdp_last_error()
     # strided: bad strides
     assert lib.tdp_solve_strided(2, 8, -1, 1, 16, 16, 16, 16, 16, 4, 0, 0, 0) == 1
-    # backward refuses the refinement dtype
-    assert lib.tdp_solve_backward(16, 1, 8, 16, 16, 16, 16, 16, 0, 0, 0, 0, 4, 2, 0) == 1
+    # backward refuses an unknown dtype
+    assert lib.tdp_solve_backward(16, 1, 8, 16, 16, 16, 16, 16, 0, 0, 0, 0, 4, 5, 0) == 1
+    assert "dtype" in tdp.tdp_last_error()
     # many right-hand sides: (a, b, c, d, x, n, nrhs, ldd, ldx, s, dtype, stream)
     m = lib.tdp_solve_multi
     assert m(16, 16, 16, 1 << 20, 1 << 24, 10, 0, 10, 10, 4, 0, 0) == 1      # nrhs < 1

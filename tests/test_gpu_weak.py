@@ -114,10 +114,13 @@ def test_weak_batched(tdp, code):
             assert e <= tol(code, KAPPA_WEAK), (Sb.batch, s, e)
 
 
-@pytest.mark.parametrize("code", [0, 1])
+@pytest.mark.parametrize("code", [0, 1, 2])
 def test_weak_adjoint(tdp, code):
     """A^T has the columns of A as rows, so these systems are made dominant by
-    columns too (by the same margin): the bound on kappa then holds for A^T."""
+    columns too (by the same margin): the bound on kappa then holds for A^T.
+    code 2 (one binary64 correction): the windowed pass rejects these rows
+    (the decay across its halo is too slow) and the exact binary64 solve
+    answers."""
     import torch
 
     sizes = [64, 3, 8192, 1000, 2]
