@@ -637,11 +637,13 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
                           stream)
     g = torch.from_numpy(W.loss_weights(Sa.n, seed=0)).to(device)
     grads = [torch.empty_like(ax) for _ in range(4)]
-    fn = lambda: tdp.tdp_solve_backward(aoff, Sa.batch, Sa.n, adev["a"], adev["b"], adev["c"], ax, g, *grads, 0,
-                                        tdp.F64, stream)
-    ms = cuda_time(fn, steps, 2, stream)
-    out["adjoint_1024x8192"] = {"ms": ms, "unknowns_per_s": Sa.n / (ms * 1e-3),
-                                "hbm_frac_72B": hbm(ms, 72 * Sa.n)}
+    res = {}
+    for name, code in (("fp64", tdp.F64), ("fp32_refine1", tdp.F32_REFINE)):
+        fn = lambda: tdp.tdp_solve_backward(aoff, Sa.batch, Sa.n, adev["a"], adev["b"], adev["c"], ax, g, *grads, 0,
+                                            code, stream)
+        ms = cuda_time(fn, steps, 2, stream)
+        res[name] = {"ms": ms, "unknowns_per_s": Sa.n / (ms * 1e-3), "hbm_frac_72B": hbm(ms, 72 * Sa.n)}
+    out["adjoint_1024x8192"] = res
     del adev, ax, grads
     # many right-hand sides of one matrix: 16 columns of a 2^22-row system,
     # one factorisation, against the same columns as 16 separate solves

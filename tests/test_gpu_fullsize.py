@@ -91,16 +91,23 @@ def test_batched_4096_log_uniform(tdp, batched_full, code):
     assert worst <= TOL[code], (code, worst)
 
 
-def test_adjoint_1024x8192(tdp):
-    import torch
-
+@pytest.fixture(scope="module")
+def adjoint_full():
     Sa = W.uniform_batch(1024, 8192, seed=0)
     x = oracle.thomas_batched(Sa.a, Sa.b, Sa.c, Sa.d, offsets=Sa.offsets)
     g = W.loss_weights(Sa.n, seed=0)
-    ref = oracle.adjoint_batched(Sa.a, Sa.b, Sa.c, x, g, Sa.offsets)
+    return Sa, x, g, oracle.adjoint_batched(Sa.a, Sa.b, Sa.c, x, g, Sa.offsets)
+
+
+@pytest.mark.parametrize("code", [0, 2])
+def test_adjoint_1024x8192(tdp, adjoint_full, code):
+    """code 2: the transposed solve in binary32 with one binary64 correction."""
+    import torch
+
+    Sa, x, g, ref = adjoint_full
     a, b, c, X, G = (_dev(v, torch.float64) for v in (Sa.a, Sa.b, Sa.c, x, g))
     outs = [torch.empty_like(X) for _ in range(4)]
-    tdp.tdp_solve_backward(torch.from_numpy(Sa.offsets).cuda(), Sa.batch, Sa.n, a, b, c, X, G, *outs, 0, 0)
+    tdp.tdp_solve_backward(torch.from_numpy(Sa.offsets).cuda(), Sa.batch, Sa.n, a, b, c, X, G, *outs, 0, code)
     torch.cuda.synchronize()
     for k, o in zip("abcd", outs):
         assert oracle.rel_err(o.cpu().numpy(), ref[k]) <= 1e-12, k
