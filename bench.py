@@ -81,15 +81,16 @@ def stage1_f64_roofline(ms, n, s, hbm_peak_gbs, traffic=None, peak_gops=None, pe
 def window_geometry(tdp):
     """(rows per thread, halo rows, owned rows per tile) of the windowed pass."""
     sw = tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW)
-    halo = max(16, min(tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO), 64)) & ~1
+    halo = max(16, min(tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO), 64)) & ~3
     return sw, halo, 256 * sw - 2 * halo
 
 
 def window_roofline(tdp, ms, n, iters, hbm_peak_gbs, fp64_peak_gops, traffic=None):
-    """HBM roofline of the windowed pass (k_window_refine) from its event-timed
-    launch: 32 bytes read and 8 written per row (algorithmic), against the
-    measured copy bandwidth; beside it the binary64 pipe: per correction
-    3 FMA per window row (the residual) and 1 add per owned row (the update)."""
+    """HBM roofline of the windowed pass (k_window<double>) from its
+    event-timed launch: 32 bytes read and 8 written per row (algorithmic),
+    against the measured copy bandwidth; beside it the binary64 pipe: per
+    correction 3 FMA per window row (the residual) and 1 add per owned row
+    (the update)."""
     sw, halo, tr = window_geometry(tdp)
     gbs = 40 * n / (ms * 1e-3) / 1e9
     ops_row = iters * (3 * (256 * sw) / tr + 1)

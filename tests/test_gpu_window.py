@@ -121,6 +121,100 @@ def test_window_batches(tdp):
             assert e <= 1e-12, (Sb.batch, iters, e)
 
 
+@pytest.mark.parametrize("k,fallback", [(-800, False), (800, False), (-1000, True), (1000, True)])
+def test_window_scaled_right_hand_side(tdp, k, fallback):
+    """d scaled by 2^k (x* with it, exactly): the window's binary32 copies of
+    d and x carry the scale 2^-m, m the exponent of the window's largest |d|,
+    so the pass answers for |m| <= 850 (a binary32 copy of d 2^-800 alone would
+    be zero) and falls back beyond; binary64 accuracy either way."""
+    n = 300_007
+    S = W.single(n, seed=29)
+    d = np.ldexp(S.d, k)
+    ref = oracle.thomas(S.a, S.b, S.c, d)
+    x, bits = solve(tdp, S.a, S.b, S.c, d, n, 1)
+    assert bool(bits & tdp.ST_FALLBACK) == fallback
+    assert oracle.rel_err(x, ref) <= 1e-12
+    assert oracle.rel_err(x, np.ldexp(S.xstar, k)) <= 1e-12
+
+
+def test_window_matrix_entries_outside_binary32_range(tdp):
+    """Off-diagonal entries below the binary32 range (every 7th row's a and
+    c times 2^-300: their binary32 copies are zero or subnormal, and the
+    binary64 residual restores them), and a whole system scaled by 2^500
+    (|b| above 1e30: every tile falls back) or 2^-500; binary64 accuracy."""
+    n = 200_003
+    S = W.single(n, seed=41)
+    a, c = S.a.copy(), S.c.copy()
+    a[::7] = np.ldexp(a[::7], -300)
+    c[::7] = np.ldexp(c[::7], -300)
+    d = W.matvec(a, S.b, c, S.xstar, S.offsets)
+    x, bits = solve(tdp, a, S.b, c, d, n, 1)
+    assert not bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, oracle.thomas(a, S.b, c, d)) <= 1e-12
+    for k in (500, -500):
+        A, B, C, D = (np.ldexp(v, k) for v in (S.a, S.b, S.c, S.d))
+        x, bits = solve(tdp, A, B, C, D, n, 1)
+        assert bits & tdp.ST_FALLBACK
+        assert oracle.rel_err(x, oracle.thomas(A, B, C, D)) <= 1e-12
+
+
+def test_window_zero_and_quiet_right_hand_sides(tdp):
+    """d = 0 gives x = 0 exactly; a system whose second half has d 2^-200
+    smaller is solved to binary64 accuracy, the quiet half (away from the
+    tile that holds both scales) to its own scale."""
+    n = 100_003
+    S = W.single(n, seed=31)
+    x, bits = solve(tdp, S.a, S.b, S.c, np.zeros(n), n, 1)
+    assert not bits & tdp.ST_FALLBACK
+    assert np.all(x == 0.0)
+    d = S.d.copy()
+    h = n // 2
+    d[h:] = np.ldexp(d[h:], -200)
+    ref = oracle.thomas(S.a, S.b, S.c, d)
+    x, bits = solve(tdp, S.a, S.b, S.c, d, n, 1)
+    assert not bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, ref) <= 1e-12
+    q = h + 2 * TILE
+    assert oracle.rel_err(x[q:], ref[q:]) <= 1e-12
+
+
+@pytest.mark.parametrize("spread,fallback", [(20, False), (300, True)])
+def test_window_batch_of_mixed_scales(tdp, spread, fallback):
+    """Systems whose right-hand sides are scaled by 2^-spread, 1, 2^spread in
+    turn, every system against the oracle on its own.  Neighbours within 2^40
+    share windows; 2^300 apart, a window that holds both falls back (the
+    smaller system's residual would fall below the binary32 range)."""
+    import torch
+
+    Sb = W.batched(64, 64, 20000, seed=33)
+    d = Sb.d.copy()
+    for j in range(Sb.batch):
+        lo, hi = int(Sb.offsets[j]), int(Sb.offsets[j + 1])
+        d[lo:hi] = np.ldexp(d[lo:hi], spread * (j % 3 - 1))
+    ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, d, offsets=Sb.offsets)
+    A, B, C, D = (dev(v) for v in (Sb.a, Sb.b, Sb.c, d))
+    x = torch.full_like(D, float("nan"))
+    tdp.tdp_solve_batched(dev(Sb.offsets), Sb.batch, Sb.n, A, B, C, D, x, 0, tdp.F32_REFINE, 1)
+    torch.cuda.synchronize()
+    assert bool(tdp.LIB.tdp_last_status_bits() & tdp.ST_FALLBACK) == fallback
+    e = per_system_err(host(x), ref, Sb.offsets)
+    assert e <= 1e-12, (spread, e)
+
+
+def test_window_update_near_binade_edges(tdp):
+    """x* of signed powers of two and zeros: the binary32 solution lies on or
+    next to the ends of its binade and at zero, where the correction is added
+    by the binary64 pipe (the integer update would leave the binade)."""
+    n = 200_003
+    S = W.binade_edges(n, seed=37)
+    ref = oracle.thomas(S.a, S.b, S.c, S.d)
+    for iters in (1, 2):
+        x, bits = solve(tdp, S.a, S.b, S.c, S.d, n, iters)
+        assert not bits & tdp.ST_FALLBACK
+        assert oracle.rel_err(x, ref) <= 1e-12
+        assert oracle.rel_err(x, S.xstar) <= 1e-12
+
+
 def test_window_bad_offsets(tdp):
     import torch
 
@@ -134,8 +228,9 @@ def test_window_bad_offsets(tdp):
 
 
 def test_window_heat_step_passes_its_bound(tdp):
-    """tdp(-r, 1 + 2r, -r) at r = 0.5: every factor of the decay bound is
-    1/2, and 48 halo rows give 2^-48 < 2^-46, so the windowed pass answers."""
+    """tridiag(-r, 1 + 2r, -r) at r = 0.5: every factor of the decay bound,
+    |a| / (|b| - |c|) = r / (1 + r), is 1/3, and 48 halo rows give
+    3^-48 < 2^-46, so the windowed pass answers."""
     n = 1 << 20
     r = 0.5
     a = np.full(n, -r)

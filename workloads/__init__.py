@@ -13,7 +13,7 @@ under seed ``seed`` is ``mix64(key + (i + 1) * GAMMA)`` with
 Uniform doubles take the top 53 bits: ``(z >> 11) * 2**-53`` in [0, 1).
 
 Streams: 0 = a, 1 = b, 2 = c, 3 = x*, 4 = system sizes, 5/6 = normal draws,
-7 = heat field.
+7 = heat field, 8/9 = exponents and zeros of ``binade_edges``.
 
 Workloads (value distributions of the benchmark configurations)
 ---------------------------------------------------------------
@@ -28,6 +28,8 @@ Workloads (value distributions of the benchmark configurations)
   Dirichlet zeros outside the grid (the solver ignores a at a line's first
   row and c at its last, so one materialised diagonal serves the row and the
   column sweep), field u ~ U[0, 1].
+* ``binade_edges``: ``single``'s matrix with x* of signed powers of two
+  2^k, k uniform in {-3, ..., 3}, and zeros (probability 1/10), d = A x*.
 * ``weak``: near-weakly-dominant systems: a, c ~ U[-1, 1] as ``single`` /
   ``batched``, b = (|a| + |c|)(1 + margin) (every row dominant by the
   relative margin only; optionally every column as well), x* ~ U[-1, 1],
@@ -44,7 +46,7 @@ GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
-STREAM_A, STREAM_B, STREAM_C, STREAM_X, STREAM_N, STREAM_G1, STREAM_G2, STREAM_U = range(8)
+STREAM_A, STREAM_B, STREAM_C, STREAM_X, STREAM_N, STREAM_G1, STREAM_G2, STREAM_U, STREAM_E, STREAM_Z = range(10)
 STREAM_RHS = 16  # right-hand-side columns use streams 16, 17, ...
 
 
@@ -164,6 +166,18 @@ def single(n: int, seed: int = 0) -> System:
     if n < 1:
         raise ValueError("n must be >= 1")
     return _values(seed, np.array([0, n], dtype=np.int64))
+
+
+def binade_edges(n: int, seed: int = 0) -> System:
+    """``single``'s matrix with a solution of signed powers of two and zeros:
+    x*_i = +-2^k, k uniform in {-3, ..., 3}, x*_i = 0 with probability 1/10."""
+    S = single(n, seed)
+    u = uniform(seed, STREAM_E, n)
+    k = np.floor(u * 14.0).astype(np.int64)  # 0..13: sign from the parity, exponent from the rest
+    x = np.ldexp(np.where(k % 2 == 0, 1.0, -1.0), k // 2 - 3)
+    x[uniform(seed, STREAM_Z, n) < 0.1] = 0.0
+    d = matvec(S.a, S.b, S.c, x, S.offsets)
+    return System(S.a, S.b, S.c, d, x, S.offsets)
 
 
 def batch_sizes(batch: int, lo: int, hi: int, seed: int = 0) -> np.ndarray:
