@@ -434,7 +434,8 @@ def run_ours(args, world, rank, local):
     host_x = torch.empty(N_MAIN, dtype=torch.float64).pin_memory()
 
     def step_e2e():
-        # the library's host-array entry: copies in, solve, copy out
+        # the library's host-array entry: the windowed pass streamed by chunks,
+        # copies in and out overlapping the solve
         tdp.tdp_solve_host(host["a"], host["b"], host["c"], host["d"], host_x, N_MAIN, 0, tdp.F32_REFINE, 1, stream)
 
     def step_e2e64():

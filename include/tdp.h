@@ -133,8 +133,13 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
  * about eight chunks, Stage 1 of a chunk while the next one is copied in,
  * Stage 3 of a chunk while the previous one is copied out (a second stream
  * that the call creates and releases); the answer is the one tdp_solve
- * gives, bit for bit.  The windowed passes (refinement and, by default,
- * binary32) copy everything in, solve and copy out.  Asynchronous on `stream` like tdp_solve: x is
+ * gives, bit for bit.  The windowed passes (the refinement and, by default,
+ * binary32) stream in about sixteen chunks of whole tiles: a chunk's tiles
+ * are solved as soon as it has been copied in, and their x is copied out on a
+ * second stream while later chunks are copied in; this needs x in memory the
+ * device can address (pinned or registered), where the exact fallback, if a
+ * tile fails, writes x directly; with pageable x these passes copy everything
+ * in, solve and copy out.  Asynchronous on `stream` like tdp_solve: x is
  * complete when the stream's work is.  The device copies of the arrays live
  * in the workspace (5n elements).  Other arguments and errors as tdp_solve;
  * x must not overlap an input. */

@@ -685,48 +685,80 @@ __global__ void k_check_offsets(const int64_t* __restrict__ off, int32_t batch, 
 // (tdp_window.cuh), followed by the exact binary64 solve of the whole system
 // in one cooperative launch that runs only when a tile failed its checks.
 // off: a batch solved as one system (nsys systems), null for one system.
+// The pass is planned once (scratch, gate word, the fallback's parameters)
+// and may be launched over consecutive ranges of tiles (the host-array solve
+// launches each range once its rows have been copied in).
 // ---------------------------------------------------------------------------
+template <typename S>
+struct WindowPlan {
+  WinParams<S> W;
+  ExactParams<S> E;
+  CoopParams P;
+  unsigned* gate;
+  int SW;
+  int64_t tiles;
+  bool live;  // scratch taken, gate cleared, offsets checked: launches may follow
+};
 
 template <typename S>
-void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
-                 const int64_t* off, int32_t nsys) {
+WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
+                          const int64_t* off, int32_t nsys) {
   constexpr bool REFINE = sizeof(S) == 8;
+  WindowPlan<S> Q;
   const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~3;
-  const int SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
-  const int TR = kWinT * SW - 2 * H;
-  const int64_t tiles = (n + TR - 1) / TR;
-  unsigned* gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
+  Q.SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
+  const int TR = kWinT * Q.SW - 2 * H;
+  Q.tiles = (n + TR - 1) / TR;
+  Q.gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
   const int64_t m0 = (n + kExS - 1) / kExS;
-  ExactParams<S> E{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
-  E.ra = ctx.ar->take<double>(2 * m0);
-  E.rb = ctx.ar->take<double>(2 * m0);
-  E.rc = ctx.ar->take<double>(2 * m0);
-  E.rd = ctx.ar->take<double>(2 * m0);
-  E.y0 = ctx.ar->take<double>(2 * m0);
-  CoopParams P;
-  coop_build(ctx, E.ra, E.rb, E.rc, E.rd, E.y0, 2 * m0, P);
-  if (ctx.dry || ctx.err != cudaSuccess) return;
-  ctx.fail(cudaMemsetAsync(gate, 0, 3 * sizeof(unsigned), ctx.stream), "gate clear");
+  Q.E = ExactParams<S>{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
+  Q.E.ra = ctx.ar->take<double>(2 * m0);
+  Q.E.rb = ctx.ar->take<double>(2 * m0);
+  Q.E.rc = ctx.ar->take<double>(2 * m0);
+  Q.E.rd = ctx.ar->take<double>(2 * m0);
+  Q.E.y0 = ctx.ar->take<double>(2 * m0);
+  coop_build(ctx, Q.E.ra, Q.E.rb, Q.E.rc, Q.E.rd, Q.E.y0, 2 * m0, Q.P);
+  // binary64 storage: the windowed solution within 2^-45 ||x|| (the refinement
+  // goes below binary32 rounding); binary32 storage: within 2^-30 ||x||
+  const float tau = REFINE ? kWinTau : 1.0f / 2147483648.0f;
+  Q.W = WinParams<S>{a, b, c, d, x, n, H, TR, REFINE ? iters : 0, tau, off, nsys, Q.gate, ctx.status,
+                     1ll << ctx.wait_log2, ctx.window_prefetch, 0};
+  Q.live = !ctx.dry && ctx.err == cudaSuccess;
+  if (!Q.live) return Q;
+  ctx.fail(cudaMemsetAsync(Q.gate, 0, 3 * sizeof(unsigned), ctx.stream), "gate clear");
   if (off) {
     pre_launch(ctx, "check_offsets");
     k_check_offsets<<<grid_for(int64_t(nsys) + 1, 256), 256, 0, ctx.stream>>>(off, nsys, n, ctx.status);
     post_launch(ctx, "offsets check");
   }
-  // binary64 storage: the windowed solution within 2^-45 ||x|| (the refinement
-  // goes below binary32 rounding); binary32 storage: within 2^-30 ||x||
-  const float tau = REFINE ? kWinTau : 1.0f / 2147483648.0f;
-  WinParams<S> W{a, b, c, d, x, n, H, TR, REFINE ? iters : 0, tau, off, nsys, gate, ctx.status,
-                 1ll << ctx.wait_log2, ctx.window_prefetch};
-  auto wk = SW == 5 ? k_window<S, 5, REFINE ? 3 : 4> : k_window<S, 7, 2>;
+  Q.live = ctx.err == cudaSuccess;
+  return Q;
+}
+
+// Tiles [t0, t1) of a planned pass.
+template <typename S>
+void window_launch(Ctx& ctx, WindowPlan<S>& Q, int64_t t0, int64_t t1) {
+  constexpr bool REFINE = sizeof(S) == 8;
+  if (!Q.live || ctx.err != cudaSuccess || t1 <= t0) return;
+  Q.W.tile0 = t0;
+  auto wk = Q.SW == 5 ? k_window<S, 5, REFINE ? 3 : 4> : k_window<S, 7, 2>;
   allow_smem(wk);
-  const char* name = REFINE ? "window_refine" : "window_f32";
-  pre_launch(ctx, name);
-  wk<<<unsigned(tiles), kWinT, SW == 5 ? WinSmem<S, 5>::bytes() : WinSmem<S, 7>::bytes(), ctx.stream>>>(W);
+  pre_launch(ctx, REFINE ? "window_refine" : "window_f32");
+  wk<<<unsigned(t1 - t0), kWinT, Q.SW == 5 ? WinSmem<S, 5>::bytes() : WinSmem<S, 7>::bytes(), ctx.stream>>>(Q.W);
   post_launch(ctx, "windowed pass");
+}
+
+// The gated exact solve after every tile has run; it writes x through xout
+// (the device array of the pass, or a device-visible alias of the caller's
+// host array).
+template <typename S>
+void window_fallback(Ctx& ctx, WindowPlan<S>& Q, S* xout) {
+  if (!Q.live || ctx.err != cudaSuccess) return;
+  Q.E.x = xout;
   // two CTAs per SM: the launch costs little when the gate is clear (every CTA
   // returns at once), and the grid-stride loops cover any size when it is set
   auto ek = k_exact_coop<S>;
-  const int grid = coop_grid(ek, 128, (std::max(m0, P.L > 0 ? P.lv[0].m : int64_t(1)) + 127) / 128, 2);
+  const int grid = coop_grid(ek, 128, (std::max(Q.E.m0, Q.P.L > 0 ? Q.P.lv[0].m : int64_t(1)) + 127) / 128, 2);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(128);
@@ -738,8 +770,103 @@ void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   pre_launch(ctx, "exact_fallback");
-  ctx.fail(cudaLaunchKernelEx(&cfg, ek, E, P, (const unsigned*)gate, gate + 1, ctx.status), "exact fallback launch");
+  ctx.fail(cudaLaunchKernelEx(&cfg, ek, Q.E, Q.P, (const unsigned*)Q.gate, Q.gate + 1, ctx.status),
+           "exact fallback launch");
   post_launch(ctx, "exact fallback");
+}
+
+template <typename S>
+void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
+                 const int64_t* off, int32_t nsys) {
+  WindowPlan<S> Q = window_plan(ctx, a, b, c, d, x, n, iters, off, nsys);
+  window_launch(ctx, Q, 0, Q.tiles);
+  window_fallback(ctx, Q, x);
+}
+
+// Host arrays through the windowed pass.  The rows are copied in by chunks of
+// whole tiles on one stream; each chunk's tiles run as soon as the chunk has
+// landed (the tile that needs the next chunk's first halo rows runs with the
+// next chunk), and their x goes out on a second stream while later chunks are
+// copied in and solved.  The gated exact solve, when a tile failed, writes x
+// straight into the caller's array after every chunk has been copied out, so
+// the array must be visible to the device (pinned or registered memory);
+// otherwise everything is copied in, solved and copied out.
+template <typename S>
+void window_host(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters, S* ad,
+                 S* bd, S* cd, S* dd, S* xd) {
+  WindowPlan<S> Q = window_plan(ctx, (const S*)ad, (const S*)bd, (const S*)cd, (const S*)dd, xd, n, iters,
+                                (const int64_t*)nullptr, 0);
+  if (!Q.live) return;
+  const S* hsrc[4] = {a, b, c, d};
+  S* dsrc[4] = {ad, bd, cd, dd};
+  S* xdev = nullptr;  // the caller's x as the device sees it
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, x) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) xdev = static_cast<S*>(pa.devicePointer);
+  } else {
+    cudaGetLastError();  // (not a CUDA pointer at all: clear the error it leaves)
+  }
+  if (!xdev) {
+    for (int i = 0; i < 4 && ctx.err == cudaSuccess; ++i)
+      ctx.fail(cudaMemcpyAsync(dsrc[i], hsrc[i], size_t(n) * sizeof(S), cudaMemcpyHostToDevice, ctx.stream),
+               "copy in");
+    window_launch(ctx, Q, 0, Q.tiles);
+    window_fallback(ctx, Q, xd);
+    if (ctx.err == cudaSuccess)
+      ctx.fail(cudaMemcpyAsync(x, xd, size_t(n) * sizeof(S), cudaMemcpyDeviceToHost, ctx.stream), "copy out");
+    return;
+  }
+  const int64_t TR = Q.W.TR, H = Q.W.H;
+  const int64_t ct = std::max<int64_t>(64, (Q.tiles + 15) / 16);  // tiles per chunk: about 16 chunks
+  const int64_t C = ct * TR;
+  const int64_t nch = (n + C - 1) / C;
+  cudaStream_t cin = nullptr, cout = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto event = [&]() {
+    cudaEvent_t e = nullptr;
+    ctx.fail(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    if (e) evs.push_back(e);
+    return e;
+  };
+  ctx.fail(cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking), "copy stream");
+  ctx.fail(cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking), "copy stream");
+  if (ctx.err == cudaSuccess) {  // the copies start after the caller's earlier work
+    cudaEvent_t go = event();
+    if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(go, ctx.stream), "event");
+    if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(cin, go, 0), "event");
+    if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(cout, go, 0), "event");
+  }
+  int64_t tdone = 0;
+  for (int64_t k = 0; k < nch && ctx.err == cudaSuccess; ++k) {
+    const int64_t r0 = k * C, r1 = std::min(n, r0 + C);
+    for (int i = 0; i < 4 && ctx.err == cudaSuccess; ++i)
+      ctx.fail(cudaMemcpyAsync(dsrc[i] + r0, hsrc[i] + r0, size_t(r1 - r0) * sizeof(S), cudaMemcpyHostToDevice,
+                               cin), "copy in");
+    cudaEvent_t ready = event();
+    if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(ready, cin), "event");
+    if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(ctx.stream, ready, 0), "event");
+    // tile t needs rows up to (t + 1) TR + H
+    const int64_t t1 = k == nch - 1 ? Q.tiles : std::max(tdone, (r1 - H) / TR);
+    if (t1 <= tdone) continue;
+    window_launch(ctx, Q, tdone, t1);
+    cudaEvent_t done = event();
+    if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(done, ctx.stream), "event");
+    if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(cout, done, 0), "event");
+    const int64_t x0 = tdone * TR, x1 = std::min(n, t1 * TR);
+    if (ctx.err == cudaSuccess)
+      ctx.fail(cudaMemcpyAsync(x + x0, xd + x0, size_t(x1 - x0) * sizeof(S), cudaMemcpyDeviceToHost, cout),
+               "copy out");
+    tdone = t1;
+  }
+  if (ctx.err == cudaSuccess) {  // every chunk of x is in place before the fallback may rewrite it
+    cudaEvent_t fin = event();
+    if (ctx.err == cudaSuccess) ctx.fail(cudaEventRecord(fin, cout), "event");
+    if (ctx.err == cudaSuccess) ctx.fail(cudaStreamWaitEvent(ctx.stream, fin, 0), "event");
+  }
+  window_fallback(ctx, Q, xdev);
+  if (cin) cudaStreamDestroy(cin);  // released once their work is done
+  if (cout) cudaStreamDestroy(cout);
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
 // ---------------------------------------------------------------------------
@@ -1224,12 +1351,14 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
 }
 
 // ---------------------------------------------------------------------------
-// Host arrays in, host array out.  The binary64 and binary32 solves are
-// pipelined over about eight chunks of whole tiles: while chunk k+1 is being
-// copied in (a second stream), Stage 1 runs on chunk k; after the interface
-// solve, chunk k's Stage 3 runs while chunk k-1 is copied out.  Tiles and
-// arithmetic are those of the one-piece solve, so the answer is the same bit
-// for bit.  Other schedules copy everything in, solve, and copy out.
+// Host arrays in, host array out.  The windowed passes (binary32 with
+// refinement, binary32) stream: see window_host.  The exact binary64 and
+// binary32 solves are pipelined over about eight chunks of whole tiles: while
+// chunk k+1 is being copied in (a second stream), Stage 1 runs on chunk k;
+// after the interface solve, chunk k's Stage 3 runs while chunk k-1 is copied
+// out.  Tiles and arithmetic are those of the one-piece solve, so the answer
+// is the same bit for bit.  Other schedules copy everything in, solve, and
+// copy out.
 // ---------------------------------------------------------------------------
 void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const void* d, void* x, int64_t n, int s,
                 tdp_dtype dt, int refine_iters) {
@@ -1245,9 +1374,16 @@ void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const voi
   char* xd = ctx.ar->take<char>(size_t(n) * el);
   const char* hsrc[4] = {(const char*)a, (const char*)b, (const char*)c, (const char*)d};
   char* dsrc[4] = {ad, bd, cd, dd};
-  // (binary32 storage takes the windowed pass, whose single read leaves no
-  // Stage 1 / Stage 3 split to pipeline the copies against)
-  const bool chunked = ctx.vtile && (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0 && !ctx.window32));
+  if (ctx.rec_mode == 0 && ((dt == TDP_F32_REFINE && ctx.window) || (dt == TDP_F32 && ctx.window32))) {
+    if (dt == TDP_F32_REFINE)
+      window_host<double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)d, (double*)x, n,
+                          refine_iters, (double*)ad, (double*)bd, (double*)cd, (double*)dd, (double*)xd);
+    else
+      window_host<float>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)d, (float*)x, n, 0,
+                         (float*)ad, (float*)bd, (float*)cd, (float*)dd, (float*)xd);
+    return;
+  }
+  const bool chunked = ctx.vtile && (dt == TDP_F64 ? s % 2 == 0 : (dt == TDP_F32 && s % 4 == 0));
   if (!chunked) {
     if (!ctx.dry && ctx.err == cudaSuccess)
       for (int i = 0; i < 4; ++i)

@@ -277,6 +277,33 @@ def test_window_falls_back_on_a_weak_region(tdp):
         tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, old)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_window_host_arrays_with_fallback(tdp, pinned):
+    """tdp_solve_host streams the windowed pass chunk by chunk; when a tile
+    fails, the exact solve rewrites x after every chunk has been copied out:
+    straight into the caller's pinned array, or through the device copy for a
+    pageable one.  A system with one weak stretch (fallback) and one without."""
+    import torch
+
+    n = 1_000_003
+    S = W.single(n, seed=43)
+    b = S.b.copy()
+    lo, hi = 700_000, 704_000
+    b[lo:hi] = (np.abs(S.a[lo:hi]) + np.abs(S.c[lo:hi])) * (1 + 1e-3)
+    d = W.matvec(S.a, b, S.c, S.xstar, S.offsets)
+    for bb, dd, fallback in ((S.b, S.d, False), (b, d, True)):
+        ref = oracle.thomas(S.a, bb, S.c, dd)
+        hs = [torch.from_numpy(np.ascontiguousarray(v)) for v in (S.a, bb, S.c, dd)]
+        hx = torch.full((n,), float("nan"), dtype=torch.float64)
+        if pinned:
+            hs = [h.pin_memory() for h in hs]
+            hx = hx.pin_memory()
+        tdp.tdp_solve_host(*hs, hx, n, 0, tdp.F32_REFINE, 1)
+        torch.cuda.synchronize()
+        assert bool(tdp.LIB.tdp_last_status_bits() & tdp.ST_FALLBACK) == fallback
+        assert oracle.rel_err(hx.numpy(), ref) <= 1e-12, (pinned, fallback)
+
+
 def test_window_fallback_timeout_reported(tdp):
     """The fallback's grid barrier made unreachable (testing key): its wait
     runs out and the call reports TDP_ETIMEOUT; with the gate clear the
