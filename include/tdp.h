@@ -306,8 +306,8 @@ int64_t tdp_launch_count(void);
                                    (each block's rows contiguous in shared memory) */
 #define TDP_TUNE_WINDOW 20      /* 1: TDP_F32_REFINE single systems and batches take the windowed single pass
                                    (see tdp_solve) */
-#define TDP_TUNE_WINDOW_HALO 21 /* halo rows on each side of a tile of the windowed pass [16, 64], rounded down
-                                   to a multiple of 4 */
+#define TDP_TUNE_WINDOW_HALO 21 /* halo rows on each side of a tile of the refinement's windowed pass [16, 64],
+                                   rounded down to a multiple of 4; default 48 */
 #define TDP_TUNE_WAIT_LOG2 22   /* every bounded device wait gives up after 2^value clock cycles [10, 40] */
 #define TDP_TUNE_WAIT_NEVER 23  /* 1 (testing only): grid barriers wait for one arrival more than the grid has,
                                    so every such wait runs out and the call reports TDP_ETIMEOUT */
@@ -317,6 +317,9 @@ int64_t tdp_launch_count(void);
                                    (binary32 solve of each window, no refinement; exact fallback) */
 #define TDP_TUNE_WINDOW_PREFETCH 26 /* the CTA of tile t of the windowed pass asks L2 for the window of tile
                                    t + value before loading its own [0, 4096], default 128; 0 = no prefetch */
+#define TDP_TUNE_WINDOW_HALO32 27 /* halo rows on each side of a tile of the binary32 windowed pass [16, 64],
+                                   default 32 (its bound, 2^-30, needs a third fewer rows than the
+                                   refinement's 2^-46) */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

@@ -705,7 +705,9 @@ WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S*
                           const int64_t* off, int32_t nsys) {
   constexpr bool REFINE = sizeof(S) == 8;
   WindowPlan<S> Q;
-  const int H = std::max(16, std::min(ctx.window_halo, 64)) & ~3;
+  // (binary32 storage asks the window for 2^-30 instead of 2^-46: a third
+  // fewer halo rows give the same decay per row)
+  const int H = std::max(16, std::min(REFINE ? ctx.window_halo : ctx.window_halo32, 64)) & ~3;
   Q.SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
   const int TR = kWinT * Q.SW - 2 * H;
   Q.tiles = (n + TR - 1) / TR;

@@ -286,31 +286,33 @@ def autotune_window(offsets, a, b, c, d, x, dtype, refine_iters=0, sw_grid=(5, 7
     """Pick the windowed pass's block shape (rows per thread, halo rows) for
     ``tdp_solve_batched`` on this batch by timing every pair (a halo too short
     for the batch's decay shows up as the time of the exact fallback), set
-    the knobs TDP_TUNE_WINDOW_SW and TDP_TUNE_WINDOW_HALO and return
-    (rows per thread, halo, ms).  Cached per (dtype, total rows, batch)."""
+    the knobs TDP_TUNE_WINDOW_SW and TDP_TUNE_WINDOW_HALO (binary32 + refinement)
+    or TDP_TUNE_WINDOW_HALO32 (binary32) and return (rows per thread, halo,
+    ms).  Cached per (dtype, total rows, batch)."""
     import paper_2510_27351_gb300 as tdp
 
     batch, total = offsets.numel() - 1, d.numel()
+    hkey = tdp.TUNE_WINDOW_HALO32 if int(dtype) == tdp.F32 else tdp.TUNE_WINDOW_HALO
     key = ("window", int(dtype), int(total), int(batch), int(refine_iters))
     if key not in _AUTOTUNE_CACHE:
-        old = (tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW), tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO))
+        old = (tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW), tdp.tdp_get_tuning(hkey))
         best = None
         try:
             for sw in sw_grid:
                 for h in halos:
                     tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, sw)
-                    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, h)
+                    tdp.tdp_set_tuning(hkey, h)
                     ms = _timed_ms(lambda: tdp.tdp_solve_batched(offsets, batch, total, a, b, c, d, x, 0, dtype,
                                                                  refine_iters), reps)
                     if best is None or ms < best[2]:
                         best = (sw, h, ms)
         finally:
             tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, old[0])
-            tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, old[1])
+            tdp.tdp_set_tuning(hkey, old[1])
         _AUTOTUNE_CACHE[key] = best
     sw, h, ms = _AUTOTUNE_CACHE[key]
     tdp.tdp_set_tuning(tdp.TUNE_WINDOW_SW, sw)
-    tdp.tdp_set_tuning(tdp.TUNE_WINDOW_HALO, h)
+    tdp.tdp_set_tuning(hkey, h)
     return sw, h, ms
 
 

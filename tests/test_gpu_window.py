@@ -61,7 +61,8 @@ def solve(tdp, a, b, c, d, n, iters):
     return host(x), tdp.LIB.tdp_last_status_bits()
 
 
-TILE = 256 * 5 - 2 * 48  # owned rows per tile at the default geometry
+TILE = 256 * 5 - 2 * 48  # owned rows per tile at the default geometry (refinement: 48 halo rows)
+TILE32 = 256 * 5 - 2 * 32  # the binary32 pass (32 halo rows)
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2])
@@ -344,8 +345,9 @@ def test_window_binary32_storage(tdp):
     window's bound is 2^-30 ||x||): tile-boundary sizes, a batch with tiny and
     empty systems, and inputs that fail the bound (fallback: the exact
     binary64 solve, rounded to binary32).  Tolerance 1e-5 against the
-    oracle's binary64 Thomas of the binary32-rounded inputs."""
-    for n in (1, 2, 3, 5, 97, TILE - 1, TILE, TILE + 1, 2 * TILE + 3, 100_003, (1 << 20) + 1):
+    oracle's binary64 Thomas of the binary32-rounded inputs.  The heat step
+    at r = 1 (decay factor 1/2 per row: 2^-32 over the 32 halo rows) passes."""
+    for n in (1, 2, 3, 5, 97, TILE32 - 1, TILE32, TILE32 + 1, 2 * TILE32 + 3, 100_003, (1 << 20) + 1):
         S = W.single(n, seed=n + 29)
         a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (S.a, S.b, S.c, S.d))
         x, bits = solve32(tdp, a, b, c, d, n)
@@ -360,4 +362,10 @@ def test_window_binary32_storage(tdp):
     a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (Sw.a, Sw.b, Sw.c, Sw.d))
     x, bits = solve32(tdp, a, b, c, d, Sw.n)
     assert bits & tdp.ST_FALLBACK
+    assert oracle.rel_err(x, oracle.thomas(a, b, c, d)) <= 1e-5
+    n = 1 << 20
+    a, b, c = np.full(n, -1.0), np.full(n, 3.0), np.full(n, -1.0)
+    d = W.uniform(9, 5, n, 0.0, 1.0).astype(np.float32).astype(np.float64)
+    x, bits = solve32(tdp, a, b, c, d, n)
+    assert not bits & tdp.ST_FALLBACK
     assert oracle.rel_err(x, oracle.thomas(a, b, c, d)) <= 1e-5
