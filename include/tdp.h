@@ -55,15 +55,20 @@ extern "C" {
  * The windowed single pass (not in the paper: for binary32 arithmetic, where
  * GB300's binary64 pipe does not bound the solve) reads the inputs once:
  * every tile of about 1200 rows is solved inside a window with 48 halo rows
- * on each side (binary32 partition solve of the window, its interface system
- * included, then for TDP_F32_REFINE the binary64 residual and corrections
- * on chip).  Each tile checks at run time that its window rows are
+ * (32 for TDP_F32) on each side (binary32 partition solve of the window, its
+ * interface system included, then for TDP_F32_REFINE the binary64 residual
+ * and corrections on chip; the binary32 copies of d, x and the residuals
+ * carry a power-of-two scale per window, so any scale of d keeps binary64
+ * accuracy).  Each tile checks at run time that its window rows are
  * diagonally dominant and that the decay of A^-1 across each halo bounds the
  * windowed solution's distance from x (by 2^-45 ||x|| for TDP_F32_REFINE,
  * 2^-30 ||x|| for TDP_F32); if any tile fails, the exact partition method
  * solves the whole system in binary64 in one further cooperative launch,
  * and the status word gets its informational fallback bit (8).  The size s
- * does not apply to the windowed pass. */
+ * does not apply to the windowed pass.  The exact TDP_F32_REFINE schedules
+ * (TDP_TUNE_WINDOW = 0, or the recursion schedule) narrow d without a scale:
+ * a system with a nonzero |d| outside [2^-70, 2^70] or |b| outside
+ * [2^-30, 2^30] is solved again by the same binary64 fallback (bit 8). */
 typedef enum { TDP_F64 = 0, TDP_F32 = 1, TDP_F32_REFINE = 2 } tdp_dtype;
 
 #define TDP_OK 0
@@ -120,8 +125,12 @@ int tdp_solve_batched(const int64_t* offsets, int32_t batch, int64_t total_n, co
  * element; x must not alias d.  The partition method with the coefficient
  * part of Stage 1 (pivots, multipliers, spike and backward coefficients)
  * computed once per call for a block of s rows; s in [2, 512] or 0 for the
- * size model.  Moves 3 words per unknown (d twice, x once); dtype and
- * refine_iters as tdp_solve. */
+ * size model.  Moves 3 words per unknown (d twice, x once); dtype as
+ * tdp_solve, except that TDP_F32_REFINE is solved in binary64 arithmetic
+ * (with the coefficient part tabulated a row costs 4 binary64 operations,
+ * less than binary32 passes with a binary64 residual and update would:
+ * the answer meets the refinement's accuracy at lower cost) and
+ * refine_iters is then ignored. */
 int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_t n, int32_t batch,
                     int64_t sys_stride, int64_t elem_stride, int32_t s, tdp_dtype dtype, int32_t refine_iters,
                     void* stream);

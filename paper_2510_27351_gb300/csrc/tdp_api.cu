@@ -560,7 +560,8 @@ int tdp_solve_const(double a, double b, double c, const void* d, void* x, int64_
   if ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(x)) % el)
     return set_error(TDP_EINVAL, std::string(fn) + ": pointer not aligned to its element");
   if (d == x) return set_error(TDP_EINVAL, std::string(fn) + ": x must not alias d");
-  const int ss2 = s ? s : std::min(512, int(predict_s(n, batch, dtype)));
+  // (TDP_F32_REFINE runs in binary64 arithmetic here: the binary64 size model)
+  const int ss2 = s ? s : std::min(512, int(predict_s(n, batch, dtype == TDP_F32 ? TDP_F32 : TDP_F64)));
   return run(stream, fn, [&](Ctx& ctx) {
     solve_const(ctx, a, b, c, d, x, n, batch, sys_stride, elem_stride, ss2, dtype, refine_iters);
   });

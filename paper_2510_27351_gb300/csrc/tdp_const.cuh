@@ -196,44 +196,5 @@ __global__ void __launch_bounds__(128) k_const_stage3(const C* __restrict__ tab,
   }
 }
 
-// r = d - A x in binary64 for constant coefficients (strided layout).
-__global__ void k_const_residual(double a, double b, double c, const double* __restrict__ d,
-                                 const double* __restrict__ x, double* __restrict__ r, int64_t n, int32_t batch,
-                                 int64_t ss, int64_t es) {
-  const int64_t total = int64_t(batch) * n;
-  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    int64_t j, i;
-    if (es != 1) {
-      j = q % batch;
-      i = q / batch;
-    } else {
-      j = q / n;
-      i = q % n;
-    }
-    const int64_t p = j * ss + i * es;
-    double acc = fma(-b, x[p], d[p]);
-    if (i > 0) acc = fma(-a, x[p - es], acc);
-    if (i < n - 1) acc = fma(-c, x[p + es], acc);
-    r[p] = acc;
-  }
-}
-
-// x += dx (strided layout).
-__global__ void k_const_update(double* __restrict__ x, const double* __restrict__ dx, int64_t n, int32_t batch,
-                               int64_t ss, int64_t es) {
-  const int64_t total = int64_t(batch) * n;
-  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    int64_t j, i;
-    if (es != 1) {
-      j = q % batch;
-      i = q / batch;
-    } else {
-      j = q / n;
-      i = q % n;
-    }
-    const int64_t p = j * ss + i * es;
-    x[p] += dx[p];
-  }
-}
 
 }  // namespace tdp

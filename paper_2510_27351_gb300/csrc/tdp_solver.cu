@@ -785,6 +785,45 @@ void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x,
   window_fallback(ctx, Q, x);
 }
 
+// The exact refinement schedules (the windowed pass switched off, or the
+// recursion schedule) narrow d and the residuals to binary32 without a scale.
+// A system outside the scales they carry, a nonzero |d| outside [2^-70, 2^70]
+// or |b| outside [2^-30, 2^30] (then |x| and the corrections stay inside the
+// binary32 normal range), sets the gate of the exact binary64 solve that runs
+// after them.  (The windowed pass scales each window instead.)
+__global__ void k_refine_range(const double* __restrict__ b, const double* __restrict__ d, int64_t n,
+                               unsigned* gate, unsigned* status) {
+  bool out = false;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned hd = unsigned(__double2hiint(d[i])) & 0x7fffffffu, ld = unsigned(__double2loint(d[i]));
+    const unsigned hb = unsigned(__double2hiint(b[i])) & 0x7fffffffu;
+    out |= ((hd | ld) != 0u && (hd < (953u << 20) || hd >= (1093u << 20))) || hb < (993u << 20) ||
+           hb >= (1053u << 20);
+  }
+  if (__syncthreads_or(out) && threadIdx.x == 0) {
+    atomicOr(gate, 1u);
+    flag(status, ST_FALLBACK);
+  }
+}
+
+struct RefineGuard {
+  Ctx& ctx;
+  WindowPlan<double> Q;
+  double* x;
+  RefineGuard(Ctx& c, const void* a, const void* b, const void* cc, const void* d, void* x_, int64_t n,
+              const int64_t* off, int32_t nsys)
+      : ctx(c), x((double*)x_) {
+    Q = window_plan(ctx, (const double*)a, (const double*)b, (const double*)cc, (const double*)d, x, n, 0, off,
+                    nsys);
+    if (!Q.live) return;
+    pre_launch(ctx, "refine_range");
+    k_refine_range<<<unsigned(std::min<int64_t>(grid_for(n, 256), 8 * sm_count())), 256, 0, ctx.stream>>>(
+        (const double*)b, (const double*)d, n, Q.gate, ctx.status);
+    post_launch(ctx, "refinement range check");
+  }
+  void finish() { window_fallback(ctx, Q, x); }
+};
+
 // Host arrays through the windowed pass.  The rows are copied in by chunks of
 // whole tiles on one stream; each chunk's tiles run as soon as the chunk has
 // landed (the tile that needs the next chunk's first halo rows runs with the
@@ -1138,33 +1177,16 @@ void solve_const(Ctx& ctx, double a, double b, double c, const void* d, void* x,
   if (batch <= 0 || n <= 0) return;
   Iface32Scope f32(ctx, dt != TDP_F64);
   if (s > n) s = int(std::max<int64_t>(2, n));
-  if (dt == TDP_F64) {
-    const_pass<double, double>(ctx, a, b, c, (const double*)d, (double*)x, n, batch, ss, es, s);
-  } else if (dt == TDP_F32) {
+  // binary64 storage: binary64 arithmetic for TDP_F32_REFINE too.  With the
+  // coefficient part tabulated, a row costs 4 binary64 operations and 3 words,
+  // which is faster than a binary32 pass, a binary64 residual, a second pass
+  // and an update (2048^2 heat step: 0.389 against 0.583 ms), and it needs no
+  // scaling of d into the binary32 range.
+  if (dt == TDP_F32)
     const_pass<float, float>(ctx, a, b, c, (const float*)d, (float*)x, n, batch, ss, es, s);
-  } else {
-    // binary32 solves on binary64 storage, binary64 residual and update
-    const double* D = (const double*)d;
-    double* X = (double*)x;
-    const int64_t span = int64_t(batch - 1) * ss + (n - 1) * es + 1;
-    double* r = ctx.ar->take<double>(refine_iters > 0 ? span : 1);
-    double* dx = ctx.ar->take<double>(refine_iters > 0 ? span : 1);
-    const_pass<double, float>(ctx, a, b, c, D, X, n, batch, ss, es, s);
-    const int64_t total = int64_t(batch) * n;
-    for (int it = 0; it < refine_iters; ++it) {
-      if (!ctx.dry && ctx.err == cudaSuccess) {
-        pre_launch(ctx, "const_residual_f64");
-        k_const_residual<<<grid_for(total, 256), 256, 0, ctx.stream>>>(a, b, c, D, X, r, n, batch, ss, es);
-        post_launch(ctx, "constant-coefficient residual");
-      }
-      const_pass<double, float>(ctx, a, b, c, r, dx, n, batch, ss, es, s);
-      if (!ctx.dry && ctx.err == cudaSuccess) {
-        pre_launch(ctx, "const_update_f64");
-        k_const_update<<<grid_for(total, 256), 256, 0, ctx.stream>>>(X, dx, n, batch, ss, es);
-        post_launch(ctx, "constant-coefficient update");
-      }
-    }
-  }
+  else
+    const_pass<double, double>(ctx, a, b, c, (const double*)d, (double*)x, n, batch, ss, es, s);
+  (void)refine_iters;
 }
 
 template <typename S, typename C>
@@ -1265,6 +1287,12 @@ void solve_single(Ctx& ctx, const void* a, const void* b, const void* c, const v
   }
   if (s > n) s = int(std::max<int64_t>(2, n));
   const int64_t m = (n + s - 1) / s;
+  if (dt == TDP_F32_REFINE) {
+    RefineGuard guard(ctx, a, b, c, d, x, n, nullptr, 0);
+    solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
+    guard.finish();
+    return;
+  }
   solve_blocks<false>(ctx, a, b, c, d, x, n, s, m, nullptr, nullptr, dt, refine_iters);
 }
 
@@ -1485,6 +1513,9 @@ void solve_host(Ctx& ctx, const void* a, const void* b, const void* c, const voi
   for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
+void solve_batched_exact(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
+                         const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters);
+
 void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                    const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
   ctx.rec_n = total_n;
@@ -1502,6 +1533,19 @@ void solve_batched(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tota
                        offsets, batch);
     return;
   }
+  if (dt == TDP_F32_REFINE) {
+    RefineGuard guard(ctx, a, b, c, d, x, total_n, offsets, batch);
+    solve_batched_exact(ctx, offsets, batch, total_n, a, b, c, d, x, s, dt, refine_iters);
+    guard.finish();
+    return;
+  }
+  solve_batched_exact(ctx, offsets, batch, total_n, a, b, c, d, x, s, dt, refine_iters);
+}
+
+// The exact schedules of tdp_solve_batched.
+void solve_batched_exact(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n, const void* a,
+                         const void* b, const void* c, const void* d, void* x, int s, tdp_dtype dt,
+                         int refine_iters) {
   const bool edges = dt == TDP_F32_REFINE && refine_iters > 0;
   if (s == 0) {
     // per-system sizes from the device predictor (TDP_PER_SYSTEM_S=1); the

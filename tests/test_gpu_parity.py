@@ -435,6 +435,25 @@ def test_constant_coefficients_vs_oracle(tdp, code):
             assert e <= TOL[code], (n, batch, layout, s, e)
 
 
+@pytest.mark.parametrize("k", [-300, 300])
+def test_constant_coefficients_at_any_scale(tdp, k):
+    """Binary64 storage (TDP_F32_REFINE runs binary64 arithmetic on the
+    constant path): d scaled by 2^k, far outside the binary32 range, solved to
+    1e-12 against Thomas on the materialised diagonals of the scaled input."""
+    import torch
+
+    a, b, c = -0.45, 2.1, -0.55
+    n, batch = 4099, 9
+    d2 = np.ldexp(W.uniform(17, 5, n * batch, -1, 1), k)
+    ref = _const_ref(a, b, c, d2, n, batch, n, 1)
+    D = dev(d2)
+    for code in (0, 2):
+        x = torch.zeros_like(D)
+        tdp.tdp_solve_const(a, b, c, D, x, n, batch, n, 1, 0, code, 1 if code == 2 else 0)
+        torch.cuda.synchronize()
+        assert oracle.rel_err(host(x), ref) <= 1e-12, code
+
+
 def test_constant_heat_step_closed_form(tdp):
     """The implicit heat step (b = 1 + 2r, a = c = -r) along rows then columns
     against the sine-basis closed form of tridiag(-r, 1+2r, -r)."""

@@ -216,6 +216,40 @@ def test_window_update_near_binade_edges(tdp):
         assert oracle.rel_err(x, S.xstar) <= 1e-12
 
 
+@pytest.mark.parametrize("knob", ["window_off", "recursion"])
+def test_exact_refinement_schedules_at_any_scale(tdp, knob):
+    """The exact refinement schedules (windowed pass off, or the paper's
+    recursion schedule) narrow d to binary32 without a scale: a system with a
+    nonzero |d| outside [2^-70, 2^70] sets the gate of the exact binary64
+    solve after them (fallback bit), single and batched; inside, no fallback."""
+    import torch
+
+    key = tdp.TUNE_WINDOW if knob == "window_off" else tdp.TUNE_RECURSION
+    old = tdp.tdp_get_tuning(key)
+    tdp.tdp_set_tuning(key, 0 if knob == "window_off" else 1)
+    try:
+        n = 200_003
+        S = W.single(n, seed=47)
+        for k, fallback in ((0, False), (-300, True), (300, True)):
+            d = np.ldexp(S.d, k)
+            x, bits = solve(tdp, S.a, S.b, S.c, d, n, 1)
+            assert bool(bits & tdp.ST_FALLBACK) == fallback, k
+            assert oracle.rel_err(x, oracle.thomas(S.a, S.b, S.c, d)) <= 1e-12, k
+        Sb = W.batched(40, 64, 9000, seed=48)
+        d = Sb.d.copy()
+        lo, hi = int(Sb.offsets[7]), int(Sb.offsets[8])
+        d[lo:hi] = np.ldexp(d[lo:hi], -200)
+        A, B, C, D = (dev(v) for v in (Sb.a, Sb.b, Sb.c, d))
+        x = torch.full_like(D, float("nan"))
+        tdp.tdp_solve_batched(dev(Sb.offsets), Sb.batch, Sb.n, A, B, C, D, x, 0, tdp.F32_REFINE, 1)
+        torch.cuda.synchronize()
+        assert tdp.LIB.tdp_last_status_bits() & tdp.ST_FALLBACK
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, d, offsets=Sb.offsets)
+        assert per_system_err(host(x), ref, Sb.offsets) <= 1e-12
+    finally:
+        tdp.tdp_set_tuning(key, old)
+
+
 def test_window_bad_offsets(tdp):
     import torch
 
