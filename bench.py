@@ -629,6 +629,25 @@ def run_variants(args, tdp, S, dev, x, stream, hbm_peak, device):
     out["thomas_gpu_single"] = {"ms_for_2^16_rows": ms, "unknowns_per_s": nt / (ms * 1e-3),
                                 "note": "one GPU thread runs sequential Thomas; rate independent of N"}
     del sl, xt
+    # the small single system N = 65536 (fits in L2: latency-bound): per solve,
+    # launched on the stream and replayed from a CUDA graph
+    Sl = W.single(1 << 16, seed=0)
+    ld = {k: torch.from_numpy(getattr(Sl, k)).to(device) for k in ("a", "b", "c", "d")}
+    lx = torch.empty(1 << 16, dtype=torch.float64, device=device)
+    lat = {}
+    for name, code, s_l, it in (("fp64_s32", tdp.F64, 32, 0), ("fp32_refine1", tdp.F32_REFINE, 0, 1)):
+        call = lambda st, code=code, s_l=s_l, it=it: tdp.tdp_solve(ld["a"], ld["b"], ld["c"], ld["d"], lx, 1 << 16,
+                                                                    s_l, code, it, st)
+        ms = cuda_time(lambda: call(stream), 50, 5, stream)
+        g = tdp.CapturedSolve(call)
+        ms_graph = cuda_time(g.replay, 50, 5, torch.cuda.current_stream())
+        del g
+        torch.cuda.synchronize()
+        err = float(np.abs(lx.cpu().numpy() - Sl.xstar).max() / np.abs(Sl.xstar).max())
+        lat[name] = {"us": 1e3 * ms, "us_graph": 1e3 * ms_graph, "unknowns_per_s_graph": (1 << 16) / (ms_graph * 1e-3),
+                     "rel_err_vs_xstar": err}
+    out["latency_65536"] = lat
+    del ld, lx
     # batched: 4096 systems, N log-uniform in [64, 65536]
     Sb = W.batched(4096, 64, 65536, seed=0)
     bdev = {k: torch.from_numpy(getattr(Sb, k)).to(device) for k in ("a", "b", "c", "d")}
