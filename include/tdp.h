@@ -320,8 +320,8 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_WAIT_LOG2 22   /* every bounded device wait gives up after 2^value clock cycles [10, 40] */
 #define TDP_TUNE_WAIT_NEVER 23  /* 1 (testing only): grid barriers wait for one arrival more than the grid has,
                                    so every such wait runs out and the call reports TDP_ETIMEOUT */
-#define TDP_TUNE_WINDOW_SW 24   /* rows per thread in the windowed pass's window: 5 or 7 (odd, so that the
-                                   threads' strided shared-memory reads avoid bank conflicts) */
+#define TDP_TUNE_WINDOW_SW 24   /* rows per thread in the refinement's windowed pass: 5 or 7 (default; odd,
+                                   so that the threads' strided shared-memory reads avoid bank conflicts) */
 #define TDP_TUNE_WINDOW32 25    /* 1: TDP_F32 single systems and batches take the windowed single pass too
                                    (binary32 solve of each window, no refinement; exact fallback) */
 #define TDP_TUNE_WINDOW_PREFETCH 26 /* the CTA of tile t of the windowed pass asks L2 for the window of tile
@@ -329,6 +329,9 @@ int64_t tdp_launch_count(void);
 #define TDP_TUNE_WINDOW_HALO32 27 /* halo rows on each side of a tile of the binary32 windowed pass [16, 64],
                                    default 32 (its bound, 2^-30, needs a third fewer rows than the
                                    refinement's 2^-46) */
+#define TDP_TUNE_WINDOW_SW32 28  /* most rows per thread of the binary32 windowed pass [5, 13], default 13: it
+                                   takes the largest odd count up to this that gives every SM three tiles,
+                                   else 5 */
 int tdp_set_tuning(int key, int value);
 int tdp_get_tuning(int key);
 

@@ -93,7 +93,8 @@ SYMBOLS = ("tdp_solve", "tdp_solve_batched", "tdp_solve_strided", "tdp_solve_bac
 (TUNE_SMEM_BUDGET, TUNE_S_REC, TUNE_S_TAIL, TUNE_VTILE, TUNE_COOP) = range(5)
 (TUNE_REFINE3, TUNE_RECURSION, TUNE_R, TUNE_SEGMENTED, TUNE_PER_SYSTEM_S, TUNE_IFACE32, TUNE_REFINE_KEPT,
  TUNE_COOP_REG, TUNE_BATCH_FLAT, TUNE_VTILE_B, TUNE_VTILE_L, TUNE_WINDOW, TUNE_WINDOW_HALO, TUNE_WAIT_LOG2,
- TUNE_WAIT_NEVER, TUNE_WINDOW_SW, TUNE_WINDOW32, TUNE_WINDOW_PREFETCH, TUNE_WINDOW_HALO32) = range(9, 28)
+ TUNE_WAIT_NEVER, TUNE_WINDOW_SW, TUNE_WINDOW32, TUNE_WINDOW_PREFETCH, TUNE_WINDOW_HALO32,
+ TUNE_WINDOW_SW32) = range(9, 29)
 RETIRED_TUNING_KEYS = (5, 6, 7, 8)
 
 

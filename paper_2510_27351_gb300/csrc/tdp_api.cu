@@ -90,8 +90,9 @@ Workspace* workspace_for(cudaStream_t st, int* dev_out) {
 // grid has, so that every such wait runs out; for testing the timeout path),
 // TDP_WINDOW_SW (rows per thread of the windowed pass's window, 5 or 7),
 // TDP_WINDOW32 (1: binary32 storage takes the windowed pass too),
-// TDP_WINDOW_PREFETCH (the windowed pass's L2 prefetch distance in tiles) and
-// TDP_WINDOW_HALO32 (the binary32 windowed pass's halo rows per side).
+// TDP_WINDOW_PREFETCH (the windowed pass's L2 prefetch distance in tiles),
+// TDP_WINDOW_HALO32 (the binary32 windowed pass's halo rows per side) and
+// TDP_WINDOW_SW32 (its most rows per thread, 5 to 13).
 // Keys 5 to 8 belonged to variants that were measured slower and removed;
 // they are rejected.
 struct Knob {
@@ -100,7 +101,7 @@ struct Knob {
   std::atomic<int> v;
   bool retired;
 };
-Knob g_knobs[28] = {
+Knob g_knobs[29] = {
     {"TDP_SMEM_BUDGET", 4096, 227 * 1024, {100 * 1024}, false},
     {"TDP_S_REC", 3, 1024, {16}, false},
     {"TDP_S_TAIL", 3, 256, {8}, false},
@@ -125,10 +126,11 @@ Knob g_knobs[28] = {
     {"TDP_WINDOW_HALO", 16, 64, {48}, false},
     {"TDP_WAIT_LOG2", 10, 40, {31}, false},
     {"TDP_WAIT_NEVER", 0, 1, {0}, false},
-    {"TDP_WINDOW_SW", 5, 7, {5}, false},
+    {"TDP_WINDOW_SW", 5, 7, {7}, false},
     {"TDP_WINDOW32", 0, 1, {1}, false},
     {"TDP_WINDOW_PREFETCH", 0, 4096, {128}, false},
     {"TDP_WINDOW_HALO32", 16, 64, {32}, false},
+    {"TDP_WINDOW_SW32", 5, 13, {13}, false},
 };
 std::once_flag g_knobs_once;
 
@@ -170,6 +172,7 @@ void load_knobs(Ctx& ctx) {
   ctx.window32 = g_knobs[TDP_TUNE_WINDOW32].v.load() != 0;
   ctx.window_prefetch = g_knobs[TDP_TUNE_WINDOW_PREFETCH].v.load();
   ctx.window_halo32 = g_knobs[TDP_TUNE_WINDOW_HALO32].v.load();
+  ctx.window_sw32 = g_knobs[TDP_TUNE_WINDOW_SW32].v.load();
 }
 
 // Run a driver twice: a dry run that sizes the workspace, then the real one.

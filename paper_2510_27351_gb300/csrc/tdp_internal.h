@@ -73,7 +73,8 @@ struct Ctx {
   int window_prefetch = 128;   // L2 prefetch distance of the windowed pass in tiles (TDP_WINDOW_PREFETCH)
   int window_halo = 48;        // its halo rows on each side of a tile (TDP_WINDOW_HALO)
   int window_halo32 = 32;      // the same for binary32 storage (TDP_WINDOW_HALO32)
-  int window_sw = 5;           // its window rows per thread, 5 or 7 (TDP_WINDOW_SW)
+  int window_sw32 = 13;        // most rows per thread of the binary32 windowed pass (TDP_WINDOW_SW32)
+  int window_sw = 7;           // the refinement's window rows per thread, 5 or 7 (TDP_WINDOW_SW)
   int wait_log2 = 31;          // bounded device waits give up after 2^wait_log2 cycles (TDP_WAIT_LOG2)
   bool wait_never = false;     // testing: grid barriers can never complete (TDP_WAIT_NEVER)
   bool coop = true;            // small interface levels in one cooperative launch (TDP_COOP=0 off)

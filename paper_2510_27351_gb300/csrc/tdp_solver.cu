@@ -708,7 +708,21 @@ WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S*
   // (binary32 storage asks the window for 2^-30 instead of 2^-46: a third
   // fewer halo rows give the same decay per row)
   const int H = std::max(16, std::min(REFINE ? ctx.window_halo : ctx.window_halo32, 64)) & ~3;
-  Q.SW = ctx.window_sw == 5 ? 5 : 7;  // window rows per thread
+  // window rows per thread: 5 or 7 for the refinement; for binary32 the
+  // largest odd count up to the knob (5 to 13) that still gives every SM
+  // three tiles (longer windows amortise the halo and the per-thread work,
+  // but a short system needs the CTAs), else 5
+  if (REFINE) {
+    Q.SW = ctx.window_sw == 5 ? 5 : 7;
+  } else {
+    const int top = std::max(5, std::min(ctx.window_sw32, 13)) | 1;
+    Q.SW = 5;
+    for (int sw = top; sw > 5; sw -= 2)
+      if ((n + kWinT * sw - 2 * H - 1) / (kWinT * sw - 2 * H) >= 3 * int64_t(sm_count())) {
+        Q.SW = sw;
+        break;
+      }
+  }
   const int TR = kWinT * Q.SW - 2 * H;
   Q.tiles = (n + TR - 1) / TR;
   Q.gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
@@ -743,10 +757,27 @@ void window_launch(Ctx& ctx, WindowPlan<S>& Q, int64_t t0, int64_t t1) {
   constexpr bool REFINE = sizeof(S) == 8;
   if (!Q.live || ctx.err != cudaSuccess || t1 <= t0) return;
   Q.W.tile0 = t0;
-  auto wk = Q.SW == 5 ? k_window<S, 5, REFINE ? 3 : 4> : k_window<S, 7, 2>;
+  void (*wk)(WinParams<S>) = k_window<S, 5, REFINE ? 3 : 4>;
+  size_t smem = WinSmem<S, 5>::bytes();
+  if (Q.SW == 7) {
+    wk = k_window<S, 7, 3>;
+    smem = WinSmem<S, 7>::bytes();
+  }
+  if constexpr (!REFINE) {  // three CTAs per SM up to 13 rows per thread
+    if (Q.SW == 9) {
+      wk = k_window<S, 9, 3>;
+      smem = WinSmem<S, 9>::bytes();
+    } else if (Q.SW == 11) {
+      wk = k_window<S, 11, 3>;
+      smem = WinSmem<S, 11>::bytes();
+    } else if (Q.SW == 13) {
+      wk = k_window<S, 13, 3>;
+      smem = WinSmem<S, 13>::bytes();
+    }
+  }
   allow_smem(wk);
   pre_launch(ctx, REFINE ? "window_refine" : "window_f32");
-  wk<<<unsigned(t1 - t0), kWinT, Q.SW == 5 ? WinSmem<S, 5>::bytes() : WinSmem<S, 7>::bytes(), ctx.stream>>>(Q.W);
+  wk<<<unsigned(t1 - t0), kWinT, smem, ctx.stream>>>(Q.W);
   post_launch(ctx, "windowed pass");
 }
 

@@ -136,9 +136,10 @@ def test_tuning_knobs_validate_and_round_trip():
             assert tdp.tdp_get_tuning(key) in (0, 1) and tdp.tdp_get_tuning(key) == v, key
         assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO) == 48
         assert tdp.tdp_get_tuning(tdp.TUNE_WAIT_LOG2) == 31
-        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW) == 5
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW) == 7
         assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_PREFETCH) == 128
         assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO32) == 32
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW32) == 13
         # the binary32 interface level is off by default: every interface
         # level of every precision runs in binary64 (the reduced system's
         # stability is what binary64 is kept for)
@@ -157,7 +158,7 @@ def test_tuning_knobs_validate_and_round_trip():
         tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, 0)
         assert tdp.tdp_get_tuning(tdp.TUNE_VTILE_L) == 0
         tdp.tdp_set_tuning(tdp.TUNE_VTILE_L, 1)
-        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_HALO32 + 1) == -1
+        assert tdp.tdp_get_tuning(tdp.TUNE_WINDOW_SW32 + 1) == -1
     finally:
         tdp.tdp_set_tuning(tdp.TUNE_S_REC, old)
 

@@ -61,8 +61,8 @@ def solve(tdp, a, b, c, d, n, iters):
     return host(x), tdp.LIB.tdp_last_status_bits()
 
 
-TILE = 256 * 5 - 2 * 48  # owned rows per tile at the default geometry (refinement: 48 halo rows)
-TILE32 = 256 * 5 - 2 * 32  # the binary32 pass (32 halo rows)
+TILE = 256 * 7 - 2 * 48  # owned rows per tile at the default geometry (refinement: 7 rows per thread, 48 halo rows)
+TILE32 = 256 * 5 - 2 * 32  # the binary32 pass on short systems (5 rows per thread, 32 halo rows)
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2])
@@ -381,7 +381,10 @@ def test_window_binary32_storage(tdp):
     binary64 solve, rounded to binary32).  Tolerance 1e-5 against the
     oracle's binary64 Thomas of the binary32-rounded inputs.  The heat step
     at r = 1 (decay factor 1/2 per row: 2^-32 over the 32 halo rows) passes."""
-    for n in (1, 2, 3, 5, 97, TILE32 - 1, TILE32, TILE32 + 1, 2 * TILE32 + 3, 100_003, (1 << 20) + 1):
+    # (longer systems take longer windows: 9 rows per thread from about 1e6
+    # rows, 11 from about 1.25e6, 13 from about 1.5e6 on 152 SMs)
+    for n in (1, 2, 3, 5, 97, TILE32 - 1, TILE32, TILE32 + 1, 2 * TILE32 + 3, 100_003, (1 << 20) + 1, 1_300_007,
+              1_500_001, (1 << 22) + 5):
         S = W.single(n, seed=n + 29)
         a, b, c, d = (v.astype(np.float32).astype(np.float64) for v in (S.a, S.b, S.c, S.d))
         x, bits = solve32(tdp, a, b, c, d, n)
