@@ -54,8 +54,9 @@ extern "C" {
  *
  * The windowed single pass (not in the paper: for binary32 arithmetic, where
  * GB300's binary64 pipe does not bound the solve) reads the inputs once:
- * every tile of about 1200 rows is solved inside a window with 48 halo rows
- * (32 for TDP_F32) on each side (binary32 partition solve of the window, its
+ * every tile of about 1700 rows (up to 3300 for TDP_F32) is solved inside a
+ * window with 48 halo rows (32 for TDP_F32) on each side (binary32
+ * partition solve of the window, its
  * interface system included, then for TDP_F32_REFINE the binary64 residual
  * and corrections on chip; the binary32 copies of d, x and the residuals
  * carry a power-of-two scale per window, so any scale of d keeps binary64
