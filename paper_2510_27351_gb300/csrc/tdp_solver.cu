@@ -1359,10 +1359,11 @@ __global__ void k_copy2(const double* __restrict__ a, const double* __restrict__
 // With a of every system's first row and c of its last row set to zero the
 // copies are the diagonals of one block-diagonal system.
 template <typename S>
-__global__ void k_cut_edges(const int64_t* __restrict__ off, int32_t batch, S* __restrict__ a2, S* __restrict__ c2) {
+__global__ void k_cut_edges(const int64_t* __restrict__ off, int32_t batch, int64_t total_n, S* __restrict__ a2,
+                            S* __restrict__ c2) {
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < batch; j += int64_t(gridDim.x) * blockDim.x) {
     const int64_t lo = off[j], hi = off[j + 1];
-    if (hi > lo) {
+    if (hi > lo && lo >= 0 && hi <= total_n) {  // (offsets out of range touch nothing; the check reports them)
       a2[lo] = S(0);
       c2[hi - 1] = S(0);
     }
@@ -1390,6 +1391,11 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
                 const void* c, const void* d, void* x, int s, tdp_dtype dt, int refine_iters) {
   if (s > total_n) s = int(std::max<int64_t>(2, total_n));
   const int64_t m = (total_n + s - 1) / s;
+  if (!ctx.dry && ctx.err == cudaSuccess) {  // invalid offsets raise ST_BADARG (the cuts below stay in range)
+    pre_launch(ctx, "check_offsets");
+    k_check_offsets<<<grid_for(int64_t(batch) + 1, 256), 256, 0, ctx.stream>>>(offsets, batch, total_n, ctx.status);
+    post_launch(ctx, "offsets check");
+  }
   const bool cut_in_tiles = dt != TDP_F32_REFINE ||
                             (refine_iters == 1 && ctx.refine3 && ctx.refine_kept);
   if (cut_in_tiles) {
@@ -1405,7 +1411,7 @@ void solve_flat(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t total_n
                                                                    total_n);
     post_launch(ctx, "copy of a and c");
     pre_launch(ctx, "cut_edges");
-    k_cut_edges<double><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, a2, c2);
+    k_cut_edges<double><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, total_n, a2, c2);
     post_launch(ctx, "cut edges");
   }
   solve_blocks<false>(ctx, a2, b, c2, d, x, total_n, s, m, nullptr, nullptr, dt, refine_iters);

@@ -66,7 +66,7 @@ __device__ __forceinline__ void tile_cut(const TileGeom& g, const int64_t* off, 
     const int64_t p = off[j];
     if (p > g.te) break;
     int t, jj;
-    if (p < g.te) {
+    if (p >= g.ts && p < g.te) {  // (the p >= ts test keeps unsorted offsets in the tile)
       owner<false>(g, int(p - g.ts), t, jj);
       A[jj * g.ld + t] = C(0);
       if (fst) fst[p - g.ts] = 1;

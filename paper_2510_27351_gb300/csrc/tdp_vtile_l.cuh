@@ -67,7 +67,7 @@ __device__ __forceinline__ void ltile_cut(int64_t ts, int64_t te, int s, int pv,
   for (int j = jb + (threadIdx.x & 31); j < nsys; j += 32) {
     const int64_t p = off[j];
     if (p > te) break;
-    if (p < te) A[pos(p)] = S(0);
+    if (p >= ts && p < te) A[pos(p)] = S(0);  // (the p >= ts test keeps unsorted offsets in the tile)
     if (p - 1 >= ts) C[pos(p - 1)] = S(0);
   }
 }

@@ -262,6 +262,32 @@ def test_window_bad_offsets(tdp):
         assert ei.value.code == tdp.EINVAL
 
 
+def test_bad_offsets_inside_large_batches(tdp):
+    """Offsets that are unsorted, past the end or negative in the middle of a
+    batch of large systems (the cut points fall inside the windows and tiles
+    of the windowed passes and of the binary64 flat batch) are reported as
+    TDP_EINVAL by every precision; the kernels' cuts stay inside their tiles."""
+    import torch
+
+    Sb = W.batched(sizes=[5000] * 8, seed=2)
+    good = Sb.offsets.copy()
+    for code, dt, iters in ((tdp.F64, torch.float64, 0), (tdp.F32, torch.float32, 0),
+                            (tdp.F32_REFINE, torch.float64, 1)):
+        A, B, C, D = (torch.from_numpy(v).to("cuda", dt) for v in (Sb.a, Sb.b, Sb.c, Sb.d))
+        x = torch.empty_like(D)
+        for j, v in ((3, 31_000), (3, 10 ** 9), (3, -7), (6, 2)):
+            bad = good.copy()
+            bad[j] = v
+            with pytest.raises(tdp.TdpError) as ei:
+                tdp.tdp_solve_batched(dev(bad), Sb.batch, Sb.n, A, B, C, D, x, 0, code, iters)
+            assert ei.value.code == tdp.EINVAL, (code, j, v)
+        x = torch.full_like(D, float("nan"))
+        tdp.tdp_solve_batched(dev(good), Sb.batch, Sb.n, A, B, C, D, x, 0, code, iters)
+        torch.cuda.synchronize()
+        ref = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=good)
+        assert per_system_err(host(x), ref, good) <= (1e-5 if code == tdp.F32 else 1e-12), code
+
+
 def test_window_heat_step_passes_its_bound(tdp):
     """tridiag(-r, 1 + 2r, -r) at r = 0.5: every factor of the decay bound,
     |a| / (|b| - |c|) = r / (1 + r), is 1/3, and 48 halo rows give
