@@ -619,7 +619,7 @@ template <typename S>
 __global__ void k_transpose(const S* __restrict__ a, const S* __restrict__ c, S* __restrict__ aT,
                             S* __restrict__ cT, int64_t n, const uint8_t* __restrict__ edge) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const uint8_t e = edge[i];
+    const uint8_t e = edge ? edge[i] : uint8_t(0);
     aT[i] = ((e & 1) || i == 0) ? S(0) : c[i - 1];
     cT[i] = ((e & 2) || i == n - 1) ? S(0) : a[i + 1];
   }
@@ -630,11 +630,25 @@ template <typename S>
 __global__ void k_grads(const S* __restrict__ lam, const S* __restrict__ x, S* __restrict__ ga, S* __restrict__ gb,
                         S* __restrict__ gc, int64_t n, const uint8_t* __restrict__ edge) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const uint8_t e = edge[i];
+    const uint8_t e = edge ? edge[i] : uint8_t(0);
     const S l = lam[i];
     if (ga) ga[i] = ((e & 1) || i == 0) ? S(0) : -l * x[i - 1];
     if (gb) gb[i] = -l * x[i];
     if (gc) gc[i] = ((e & 2) || i == n - 1) ? S(0) : -l * x[i + 1];
+  }
+}
+
+// The same gradients with no edge array (edge == null): every row takes its
+// neighbours; k_grad_cuts then zeroes grad_a of every system's first row and
+// grad_c of its last row.
+__global__ void k_grad_cuts(const int64_t* __restrict__ off, int32_t batch, int64_t n, double* __restrict__ ga,
+                            double* __restrict__ gc) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < batch; j += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t lo = off[j], hi = off[j + 1];
+    if (hi > lo && lo >= 0 && hi <= n) {  // (offsets out of range touch nothing; the offsets check reports them)
+      if (ga) ga[lo] = 0.0;
+      if (gc) gc[hi - 1] = 0.0;
+    }
   }
 }
 
@@ -696,15 +710,17 @@ struct WindowPlan {
   CoopParams P;
   unsigned* gate;
   int SW;
+  bool trans;  // A^T x = d (the transposed windows, k_window<..., true>)
   int64_t tiles;
   bool live;  // scratch taken, gate cleared, offsets checked: launches may follow
 };
 
 template <typename S>
 WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
-                          const int64_t* off, int32_t nsys) {
+                          const int64_t* off, int32_t nsys, bool trans = false) {
   constexpr bool REFINE = sizeof(S) == 8;
   WindowPlan<S> Q;
+  Q.trans = REFINE && trans;
   // (binary32 storage asks the window for 2^-30 instead of 2^-46: a third
   // fewer halo rows give the same decay per row)
   const int H = std::max(16, std::min(REFINE ? ctx.window_halo : ctx.window_halo32, 64)) & ~3;
@@ -727,7 +743,7 @@ WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S*
   Q.tiles = (n + TR - 1) / TR;
   Q.gate = ctx.ar->take<unsigned>(4);  // the gate word, then the fallback's grid barrier
   const int64_t m0 = (n + kExS - 1) / kExS;
-  Q.E = ExactParams<S>{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr};
+  Q.E = ExactParams<S>{a, b, c, d, x, n, m0, off, nsys, nullptr, nullptr, nullptr, nullptr, nullptr, Q.trans};
   Q.E.ra = ctx.ar->take<double>(2 * m0);
   Q.E.rb = ctx.ar->take<double>(2 * m0);
   Q.E.rc = ctx.ar->take<double>(2 * m0);
@@ -762,6 +778,12 @@ void window_launch(Ctx& ctx, WindowPlan<S>& Q, int64_t t0, int64_t t1) {
   if (Q.SW == 7) {
     wk = k_window<S, 7, 3>;
     smem = WinSmem<S, 7>::bytes();
+  }
+  if constexpr (REFINE) {
+    if (Q.trans) {
+      wk = Q.SW == 7 ? k_window<S, 7, 3, true> : k_window<S, 5, 3, true>;
+      smem = Q.SW == 7 ? WinSmem<S, 7, true>::bytes() : WinSmem<S, 5, true>::bytes();
+    }
   }
   if constexpr (!REFINE) {  // three CTAs per SM up to 13 rows per thread
     if (Q.SW == 9) {
@@ -810,8 +832,8 @@ void window_fallback(Ctx& ctx, WindowPlan<S>& Q, S* xout) {
 
 template <typename S>
 void window_pass(Ctx& ctx, const S* a, const S* b, const S* c, const S* d, S* x, int64_t n, int iters,
-                 const int64_t* off, int32_t nsys) {
-  WindowPlan<S> Q = window_plan(ctx, a, b, c, d, x, n, iters, off, nsys);
+                 const int64_t* off, int32_t nsys, bool trans = false) {
+  WindowPlan<S> Q = window_plan(ctx, a, b, c, d, x, n, iters, off, nsys, trans);
   window_launch(ctx, Q, 0, Q.tiles);
   window_fallback(ctx, Q, x);
 }
@@ -1676,15 +1698,23 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
   ctx.rec_dt = dt;
   if (batch <= 0 || total_n <= 0) return;
   const size_t el = (dt == TDP_F32) ? 4 : 8;
-  uint8_t* edge = ctx.ar->take<uint8_t>(total_n);
-  char* aT = ctx.ar->take<char>(total_n * el);
-  char* cT = ctx.ar->take<char>(total_n * el);
+  // binary32 + refinement on the windowed pass: its windows read A^T's
+  // diagonals straight from a and c (no transposed copies)
+  const bool win = dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0 && !ctx.per_system_s;
+  uint8_t* edge = win ? nullptr : ctx.ar->take<uint8_t>(total_n);  // (system ends, for the transposed copies)
+  char* aT = win ? nullptr : ctx.ar->take<char>(total_n * el);
+  char* cT = win ? nullptr : ctx.ar->take<char>(total_n * el);
   char* lam = gd ? (char*)gd : ctx.ar->take<char>(total_n * el);
-  if (!ctx.dry && ctx.err == cudaSuccess) {
+  if (!win && !ctx.dry && ctx.err == cudaSuccess) {
     ctx.fail(cudaMemsetAsync(edge, 0, size_t(total_n), ctx.stream), "edge clear");
     pre_launch(ctx, "edges");
     k_edges<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, edge, total_n);
     post_launch(ctx, "edges");
+  }
+  if (win) {
+    window_pass<double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)g, (double*)lam,
+                        total_n, 1, offsets, batch, true);
+  } else if (!ctx.dry && ctx.err == cudaSuccess) {
     pre_launch(ctx, "transpose");
     if (el == 8)
       k_transpose<double><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const double*)a, (const double*)c,
@@ -1698,7 +1728,7 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
   // so the batch is one block-diagonal tridiagonal system of total_n rows:
   // it takes the single-system path (no block map; 16-byte tiles).
   // (binary32 + refinement: one binary64 correction)
-  solve_single(ctx, aT, b, cT, g, lam, total_n, s, dt, dt == TDP_F32_REFINE ? 1 : 0);
+  if (!win) solve_single(ctx, aT, b, cT, g, lam, total_n, s, dt, dt == TDP_F32_REFINE ? 1 : 0);
   if (!ctx.dry && ctx.err == cudaSuccess && (ga || gb || gc)) {
     pre_launch(ctx, "gradients");
     if (el == 8)
@@ -1709,6 +1739,12 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
       k_grads<float><<<grid_for(total_n, 256), 256, 0, ctx.stream>>>((const float*)lam, (const float*)x, (float*)ga,
                                                                      (float*)gb, (float*)gc, total_n, edge);
     post_launch(ctx, "gradients");
+    if (win && (ga || gc)) {
+      pre_launch(ctx, "gradient_cuts");
+      k_grad_cuts<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, total_n, (double*)ga,
+                                                                          (double*)gc);
+      post_launch(ctx, "gradient cuts");
+    }
   }
 }
 

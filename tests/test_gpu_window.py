@@ -102,6 +102,40 @@ def test_window_matches_exact_schedule(tdp):
     assert oracle.rel_err(xw, S.xstar) <= 1e-12
 
 
+def test_window_adjoint_reads_transposed_windows(tdp):
+    """The adjoint of binary32 + one correction solves A^T lambda = g on the
+    windowed pass, whose windows read A^T's diagonals straight from a and c
+    (c one row early, a one row late, cut at every system's ends): batches of
+    uneven sizes, tiny systems at tile and halo boundaries, and one system of
+    many tiles, against the oracle's gradients per system and against the
+    exact schedule (TDP_TUNE_WINDOW = 0, transposed copies)."""
+    import torch
+
+    for sizes in ([5000, 1, 2, 3, 1697, 1696, 1695, 48, 47, 3000, 64],
+                  [1_000_003], list(W.batched(600, 2, 20000, seed=12).offsets[1:] - W.batched(600, 2, 20000,
+                                                                                           seed=12).offsets[:-1])):
+        Sb = W.batched(sizes=[int(v) for v in sizes], seed=13)
+        x = oracle.thomas_batched(Sb.a, Sb.b, Sb.c, Sb.d, offsets=Sb.offsets)
+        g = W.loss_weights(Sb.n, seed=13)
+        ref = oracle.adjoint_batched(Sb.a, Sb.b, Sb.c, x, g, Sb.offsets)
+        a, b, c, X, G = (dev(v) for v in (Sb.a, Sb.b, Sb.c, x, g))
+        got = {}
+        for win in (1, 0):
+            tdp.tdp_set_tuning(tdp.TUNE_WINDOW, win)
+            try:
+                outs = [torch.full_like(X, float("nan")) for _ in range(4)]
+                tdp.tdp_solve_backward(dev(Sb.offsets), Sb.batch, Sb.n, a, b, c, X, G, *outs, 0, tdp.F32_REFINE)
+                torch.cuda.synchronize()
+            finally:
+                tdp.tdp_set_tuning(tdp.TUNE_WINDOW, 1)
+            if win:
+                assert not tdp.LIB.tdp_last_status_bits() & tdp.ST_FALLBACK
+            got[win] = [host(o) for o in outs]
+        for k, o1, o0 in zip("abcd", got[1], got[0]):
+            assert per_system_err(o1, ref[k], Sb.offsets) <= 1e-12, (len(sizes), k)
+            assert per_system_err(o0, ref[k], Sb.offsets) <= 1e-12, (len(sizes), k)
+
+
 def test_window_batches(tdp):
     """Batches solved as one system through the windowed pass: log-uniform
     sizes, and tiny, one-row and empty systems (cut points inside windows and
