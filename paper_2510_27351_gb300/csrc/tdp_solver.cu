@@ -712,7 +712,7 @@ struct WindowPlan {
   int SW;
   bool trans;  // A^T x = d (the transposed windows, k_window<..., true>)
   int64_t tiles;
-  bool live;  // scratch taken, gate cleared, offsets checked: launches may follow
+  bool live;  // scratch taken, gate cleared: launches may follow
 };
 
 template <typename S>
@@ -757,12 +757,8 @@ WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S*
                      1ll << ctx.wait_log2, ctx.window_prefetch, 0};
   Q.live = !ctx.dry && ctx.err == cudaSuccess;
   if (!Q.live) return Q;
+  // (a batch's offsets are checked by the gated fallback, launched after the pass)
   ctx.fail(cudaMemsetAsync(Q.gate, 0, 3 * sizeof(unsigned), ctx.stream), "gate clear");
-  if (off) {
-    pre_launch(ctx, "check_offsets");
-    k_check_offsets<<<grid_for(int64_t(nsys) + 1, 256), 256, 0, ctx.stream>>>(off, nsys, n, ctx.status);
-    post_launch(ctx, "offsets check");
-  }
   Q.live = ctx.err == cudaSuccess;
   return Q;
 }
