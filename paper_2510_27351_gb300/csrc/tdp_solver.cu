@@ -678,6 +678,60 @@ __global__ void k_scatter(const S* __restrict__ src, S* __restrict__ dst, int32_
   }
 }
 
+// The same for the interleaved layout (sys_stride 1: element i of system j at
+// j + i es, the column sweep of an ADI step), where reading along a system
+// strides by es: a 32 x 32 tile of (system, element) passes through shared
+// memory, read along the systems and written along the elements (and the
+// reverse for the scatter), so that both sides are coalesced; up to four
+// arrays per launch.
+template <typename S>
+struct Strided4 {
+  const S* src[4];
+  S* dst[4];
+  int na;
+};
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_gather_t(const __grid_constant__ Strided4<S> G, int32_t batch, int64_t n,
+                                                  int64_t es) {
+  __shared__ S tile[32][33];
+  const int64_t j0 = int64_t(blockIdx.x) * 32, i0 = int64_t(blockIdx.y) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = 0; k < G.na; ++k) {
+#pragma unroll
+    for (int r = 0; r < 32; r += 8) {  // read along the systems
+      const int64_t j = j0 + tx, i = i0 + ty + r;
+      if (j < batch && i < n) tile[ty + r][tx] = G.src[k][j + i * es];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; r += 8) {  // write along the elements
+      const int64_t j = j0 + ty + r, i = i0 + tx;
+      if (j < batch && i < n) G.dst[k][j * n + i] = tile[tx][ty + r];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_scatter_t(const S* __restrict__ src, S* __restrict__ dst, int32_t batch,
+                                                   int64_t n, int64_t es) {
+  __shared__ S tile[32][33];
+  const int64_t j0 = int64_t(blockIdx.x) * 32, i0 = int64_t(blockIdx.y) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 32; r += 8) {  // read along the elements
+    const int64_t j = j0 + ty + r, i = i0 + tx;
+    if (j < batch && i < n) tile[ty + r][tx] = src[j * n + i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 32; r += 8) {  // write along the systems
+    const int64_t j = j0 + tx, i = i0 + ty + r;
+    if (j < batch && i < n) dst[j + i * es] = tile[tx][ty + r];
+  }
+}
+
 unsigned grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16)));
@@ -1661,7 +1715,31 @@ void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, c
     return;
   }
   const void* src[4] = {a, b, c, d};
-  if (!ctx.dry && ctx.err == cudaSuccess) {
+  // the interleaved layout (sys_stride 1) by tiled transposes, one launch for the
+  // four arrays (grid: 32 systems x 32 elements per CTA)
+  const bool tiled = ss == 1 && es >= batch && (n + 31) / 32 <= 65535;
+  const dim3 tgrid(unsigned((batch + 31) / 32), unsigned((n + 31) / 32));
+  if (tiled && !ctx.dry && ctx.err == cudaSuccess) {
+    pre_launch(ctx, "gather");
+    if (el == 8) {
+      Strided4<double> G{};
+      for (int i = 0; i < 4; ++i) {
+        G.src[i] = (const double*)src[i];
+        G.dst[i] = (double*)g[i];
+      }
+      G.na = 4;
+      k_gather_t<double><<<tgrid, 256, 0, ctx.stream>>>(G, batch, n, es);
+    } else {
+      Strided4<float> G{};
+      for (int i = 0; i < 4; ++i) {
+        G.src[i] = (const float*)src[i];
+        G.dst[i] = (float*)g[i];
+      }
+      G.na = 4;
+      k_gather_t<float><<<tgrid, 256, 0, ctx.stream>>>(G, batch, n, es);
+    }
+    post_launch(ctx, "gather");
+  } else if (!ctx.dry && ctx.err == cudaSuccess) {
     for (int i = 0; i < 4; ++i) {
       pre_launch(ctx, "gather");
       if (el == 8)
@@ -1674,7 +1752,14 @@ void solve_strided(Ctx& ctx, int32_t batch, int64_t n, int64_t ss, int64_t es, c
     }
   }
   solve_batched(ctx, off, batch, total, g[0], g[1], g[2], g[3], g[4], s, dt, refine_iters);
-  if (!ctx.dry && ctx.err == cudaSuccess) {
+  if (tiled && !ctx.dry && ctx.err == cudaSuccess) {
+    pre_launch(ctx, "scatter");
+    if (el == 8)
+      k_scatter_t<double><<<tgrid, 256, 0, ctx.stream>>>((const double*)g[4], (double*)x, batch, n, es);
+    else
+      k_scatter_t<float><<<tgrid, 256, 0, ctx.stream>>>((const float*)g[4], (float*)x, batch, n, es);
+    post_launch(ctx, "scatter");
+  } else if (!ctx.dry && ctx.err == cudaSuccess) {
     pre_launch(ctx, "scatter");
     if (el == 8)
       k_scatter<double><<<grid_for(total, 256), 256, 0, ctx.stream>>>((const double*)g[4], (double*)x, batch, n, ss,

@@ -244,6 +244,34 @@ def test_strided_heat_step(tdp, code):
 
 
 @pytest.mark.parametrize("code", [0, 1, 2])
+def test_strided_layouts(tdp, code):
+    """Strided batches beyond the square grid: the interleaved layout (element
+    i of system j at j + i*es, gathered by tiled transposes) with ragged tiles
+    (37 systems of 1000 rows, es = 37 and es = 40 with padding), and a padded
+    row-major layout (j*ss + i, ss = n + 3); every system against the oracle."""
+    import torch
+
+    dt = torch.float32 if code == 1 else torch.float64
+    for batch, n, ss, es in ((37, 1000, 1, 37), (37, 1000, 1, 40), (5, 3001, 3004, 1), (64, 33, 1, 64)):
+        size = (batch - 1) * ss + (n - 1) * es + 1
+        S = W.batched(sizes=[n] * batch, seed=batch + n)
+        arrs = []
+        for v, fill in ((S.a, 0.0), (S.b, 1.0), (S.c, 0.0), (S.d, 0.0)):
+            buf = np.full(size, fill)
+            for j in range(batch):
+                buf[j * ss + np.arange(n) * es] = v[j * n:(j + 1) * n]
+            arrs.append(torch.from_numpy(buf).to("cuda", dt))
+        x = torch.full((size,), float("nan"), dtype=dt, device="cuda")
+        tdp.tdp_solve_strided(batch, n, ss, es, *arrs, x, 0, code, 1 if code == 2 else 0)
+        torch.cuda.synchronize()
+        xs = host(x)
+        ref = oracle.thomas_batched(S.a, S.b, S.c, S.d, offsets=S.offsets)
+        for j in range(batch):
+            got = xs[j * ss + np.arange(n) * es]
+            assert oracle.rel_err(got, ref[j * n:(j + 1) * n]) <= TOL[code], (batch, n, ss, es, j)
+
+
+@pytest.mark.parametrize("code", [0, 1, 2])
 def test_backward_vs_oracle(tdp, code):
     """code 2: binary64 arrays, the transposed solve in binary32 with one
     binary64 correction (the windowed pass)."""
