@@ -641,13 +641,14 @@ __global__ void k_grads(const S* __restrict__ lam, const S* __restrict__ x, S* _
 // The same gradients with no edge array (edge == null): every row takes its
 // neighbours; k_grad_cuts then zeroes grad_a of every system's first row and
 // grad_c of its last row.
-__global__ void k_grad_cuts(const int64_t* __restrict__ off, int32_t batch, int64_t n, double* __restrict__ ga,
-                            double* __restrict__ gc) {
+template <typename S>
+__global__ void k_grad_cuts(const int64_t* __restrict__ off, int32_t batch, int64_t n, S* __restrict__ ga,
+                            S* __restrict__ gc) {
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < batch; j += int64_t(gridDim.x) * blockDim.x) {
     const int64_t lo = off[j], hi = off[j + 1];
     if (hi > lo && lo >= 0 && hi <= n) {  // (offsets out of range touch nothing; the offsets check reports them)
-      if (ga) ga[lo] = 0.0;
-      if (gc) gc[hi - 1] = 0.0;
+      if (ga) ga[lo] = S(0);
+      if (gc) gc[hi - 1] = S(0);
     }
   }
 }
@@ -774,7 +775,7 @@ WindowPlan<S> window_plan(Ctx& ctx, const S* a, const S* b, const S* c, const S*
                           const int64_t* off, int32_t nsys, bool trans = false) {
   constexpr bool REFINE = sizeof(S) == 8;
   WindowPlan<S> Q;
-  Q.trans = REFINE && trans;
+  Q.trans = trans;
   // (binary32 storage asks the window for 2^-30 instead of 2^-46: a third
   // fewer halo rows give the same decay per row)
   const int H = std::max(16, std::min(REFINE ? ctx.window_halo : ctx.window_halo32, 64)) & ~3;
@@ -845,6 +846,15 @@ void window_launch(Ctx& ctx, WindowPlan<S>& Q, int64_t t0, int64_t t1) {
     } else if (Q.SW == 13) {
       wk = k_window<S, 13, 3>;
       smem = WinSmem<S, 13>::bytes();
+    }
+    if (Q.trans) {  // the same geometry on transposed windows
+      switch (Q.SW) {
+        case 7: wk = k_window<S, 7, 3, true>; smem = WinSmem<S, 7, true>::bytes(); break;
+        case 9: wk = k_window<S, 9, 3, true>; smem = WinSmem<S, 9, true>::bytes(); break;
+        case 11: wk = k_window<S, 11, 3, true>; smem = WinSmem<S, 11, true>::bytes(); break;
+        case 13: wk = k_window<S, 13, 3, true>; smem = WinSmem<S, 13, true>::bytes(); break;
+        default: wk = k_window<S, 5, 4, true>; smem = WinSmem<S, 5, true>::bytes(); break;
+      }
     }
   }
   allow_smem(wk);
@@ -1781,7 +1791,8 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
   const size_t el = (dt == TDP_F32) ? 4 : 8;
   // binary32 + refinement on the windowed pass: its windows read A^T's
   // diagonals straight from a and c (no transposed copies)
-  const bool win = dt == TDP_F32_REFINE && ctx.window && ctx.rec_mode == 0 && !ctx.per_system_s;
+  const bool win = ctx.rec_mode == 0 && !ctx.per_system_s &&
+                   ((dt == TDP_F32_REFINE && ctx.window) || (dt == TDP_F32 && ctx.window32));
   uint8_t* edge = win ? nullptr : ctx.ar->take<uint8_t>(total_n);  // (system ends, for the transposed copies)
   char* aT = win ? nullptr : ctx.ar->take<char>(total_n * el);
   char* cT = win ? nullptr : ctx.ar->take<char>(total_n * el);
@@ -1792,7 +1803,10 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
     k_edges<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, edge, total_n);
     post_launch(ctx, "edges");
   }
-  if (win) {
+  if (win && dt == TDP_F32) {
+    window_pass<float>(ctx, (const float*)a, (const float*)b, (const float*)c, (const float*)g, (float*)lam, total_n,
+                       0, offsets, batch, true);
+  } else if (win) {
     window_pass<double>(ctx, (const double*)a, (const double*)b, (const double*)c, (const double*)g, (double*)lam,
                         total_n, 1, offsets, batch, true);
   } else if (!ctx.dry && ctx.err == cudaSuccess) {
@@ -1822,8 +1836,12 @@ void solve_backward(Ctx& ctx, const int64_t* offsets, int32_t batch, int64_t tot
     post_launch(ctx, "gradients");
     if (win && (ga || gc)) {
       pre_launch(ctx, "gradient_cuts");
-      k_grad_cuts<<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, total_n, (double*)ga,
-                                                                          (double*)gc);
+      if (el == 8)
+        k_grad_cuts<double><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, total_n,
+                                                                                  (double*)ga, (double*)gc);
+      else
+        k_grad_cuts<float><<<unsigned((batch + 255) / 256), 256, 0, ctx.stream>>>(offsets, batch, total_n,
+                                                                                 (float*)ga, (float*)gc);
       post_launch(ctx, "gradient cuts");
     }
   }
