@@ -197,9 +197,10 @@ int tdp_solve_strided(int32_t batch, int64_t n, int64_t sys_stride, int64_t elem
  * so the whole batch is solved as one system of total_n rows; s (0 = the size
  * model for one system of total_n rows) partitions that system.
  * dtype TDP_F64, TDP_F32 or TDP_F32_REFINE (binary64 arrays; the transposed
- * solve in binary32 with one binary64 correction, by the windowed pass by
- * default, whose windows read A^T's diagonals straight from a and c, so that
- * no transposed copies are written and s is not used). */
+ * solve in binary32 with one binary64 correction).  TDP_F32 and
+ * TDP_F32_REFINE run the windowed passes by default, whose windows read A^T's
+ * diagonals straight from a and c: no transposed copies are written and s is
+ * not used. */
 int tdp_solve_backward(const int64_t* offsets, int32_t batch, int64_t total_n, const void* a, const void* b,
                        const void* c, const void* x, const void* g, void* grad_a, void* grad_b, void* grad_c,
                        void* grad_d, int32_t s, tdp_dtype dtype, void* stream);
